@@ -1,0 +1,253 @@
+"""Dense brute-force oracle: the S_N-DG variational problems assembled and solved directly.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Tiny meshes only: the full space V_h has
+n_Omega * n_x * 4 unknowns and the matrix is dense.
+
+What it computes (paper sections cited per function):
+
+* standard S_N-DG, eq-sndg-scheme: find psi in V_h with B(psi, v) = Q_alpha(v) for all v in V_h;
+* low-memory LMDG, eq-gene-scheme: the same with trial = test = V_h^lm = V_{h,0} + D_{h,1} (Section 3.2);
+* reconstructed RLMDG, eq-rlmdg-vari: find psi in V_h^lm with B(psi + R*_alpha psi, v) = Q_alpha(v) for all v
+  in V_h^lm (Section 3.3); the affine part of R*_alpha is moved to the right-hand side.
+
+Entries follow Appendix A: L carries the factor w_l, S = M P has entries w_l w_l' int sigma_s/eps b b, and
+Q carries w_l.  Every integral is evaluated with 3-point Gauss-Legendre rules on the physical cell or face
+(exact for the polynomial integrands), from basis functions evaluated pointwise.
+"""
+import numpy as np
+
+_G, _GW = np.polynomial.legendre.leggauss(3)
+
+
+def _basis(xi, eta):
+    """Legendre Q1 basis (b0, b1, b2, b3) = (1, xi, eta, xi*eta) at reference points."""
+    xi = np.asarray(xi, dtype=float)
+    eta = np.asarray(eta, dtype=float)
+    return np.stack([np.ones_like(xi), xi, eta, xi * eta])
+
+
+def _basis_grad(xi, eta, h):
+    """Physical gradients (d/dx, d/dy) of the basis: d/dx = (2/h) d/dxi."""
+    xi = np.asarray(xi, dtype=float)
+    eta = np.asarray(eta, dtype=float)
+    z = np.zeros_like(xi)
+    o = np.ones_like(xi)
+    dx = np.stack([z, o, z, eta]) * (2.0 / h)
+    dy = np.stack([z, z, o, xi]) * (2.0 / h)
+    return dx, dy
+
+
+def _ref_integrals(h):
+    """Cell and face integrals of the basis on a square cell of side h (Appendix A building blocks).
+
+    mass[r][s]  = int_K b_s b_r dx
+    vol[d][r][s] = int_K b_s d_d b_r dx            (d = x, y)
+    face f in (W, E, S, N) with outward normal nu_f:
+      self[f][r][s] = int_F b_s^K b_r^K ds         (both traces from inside K)
+      nbr[f][r][s]  = int_F b_s^K' b_r^K ds        (K' = neighbour across F)
+    """
+    XI, ETA = np.meshgrid(_G, _G, indexing="ij")
+    WW = np.outer(_GW, _GW) * (h * h / 4.0)
+    B = _basis(XI, ETA)
+    dX, dY = _basis_grad(XI, ETA, h)
+    mass = np.einsum("rab,sab,ab->rs", B, B, WW)
+    vol = np.stack([np.einsum("rab,sab,ab->rs", dX, B, WW), np.einsum("rab,sab,ab->rs", dY, B, WW)])
+    fw = _GW * (h / 2.0)
+    # (own reference coordinates on the face, neighbour's reference coordinates on the same points)
+    faces = {
+        0: ((-np.ones(3), _G), (np.ones(3), _G)),     # west: own xi=-1, neighbour's xi=+1
+        1: ((np.ones(3), _G), (-np.ones(3), _G)),     # east
+        2: ((_G, -np.ones(3)), (_G, np.ones(3))),     # south
+        3: ((_G, np.ones(3)), (_G, -np.ones(3))),     # north
+    }
+    selfF = np.zeros((4, 4, 4))
+    nbrF = np.zeros((4, 4, 4))
+    for f, (own, nb) in faces.items():
+        Bo = _basis(*own)
+        Bn = _basis(*nb)
+        selfF[f] = np.einsum("ra,sa,a->rs", Bo, Bo, fw)
+        nbrF[f] = np.einsum("ra,sa,a->rs", Bo, Bn, fw)
+    normals = np.array([[-1.0, 0.0], [1.0, 0.0], [0.0, -1.0], [0.0, 1.0]])
+    return mass, vol, selfF, nbrF, normals
+
+
+def _neighbour(n, i, j, f):
+    if f == 0:
+        return (i - 1, j) if i > 0 else None
+    if f == 1:
+        return (i + 1, j) if i < n - 1 else None
+    if f == 2:
+        return (i, j - 1) if j > 0 else None
+    return (i, j + 1) if j < n - 1 else None
+
+
+def _face_alpha_integrals(alpha_l, n, i, j, f, h):
+    """int_F alpha b_r^K ds for the boundary face f of cell (i, j); alpha = a0 + a1 t along the face."""
+    if f in (0, 1):
+        a0, a1 = alpha_l[f, j]
+        t = _G                                            # t follows +y, the cell's eta on this face
+        xi = -np.ones(3) if f == 0 else np.ones(3)
+        B = _basis(xi, _G)
+    else:
+        a0, a1 = alpha_l[f, i]
+        t = _G
+        eta = -np.ones(3) if f == 2 else np.ones(3)
+        B = _basis(_G, eta)
+    return B @ ((a0 + a1 * t) * _GW) * (h / 2.0)
+
+
+def assemble(p):
+    """Global matrices of Appendix A on the full space V_h: returns (Lmat, Smat, Qvec) with B = L - S.
+
+    Index of the basis function xi^{l,p,r}: (l * n_x + p) * 4 + r, cell p = j * n + i.
+    """
+    n, h, nx, na = p.n, p.h, p.nx, p.nang
+    mass, vol, selfF, nbrF, normals = _ref_integrals(h)
+    sig_t = p.sigma_s / p.eps + p.eps * p.sigma_a
+    dim = na * nx * 4
+    L = np.zeros((dim, dim))
+    S = np.zeros((dim, dim))
+    Q = np.zeros(dim)
+    for l in range(na):
+        om = np.array([p.ox[l], p.oy[l]])
+        wl = p.w[l]
+        for j in range(n):
+            for i in range(n):
+                K = j * n + i
+                rows = slice((l * nx + K) * 4, (l * nx + K) * 4 + 4)
+                # volume: -int u Omega.grad v + int sigma_t u v   (eq-Ljk)
+                L[rows, rows] += wl * (-(om[0] * vol[0] + om[1] * vol[1]) + sig_t[K] * mass)
+                for f in range(4):
+                    on = om @ normals[f]
+                    nb = _neighbour(n, i, j, f)
+                    if on > 0:                             # outflow: upwind trace is the interior one
+                        L[rows, rows] += wl * on * selfF[f]
+                    elif nb is not None:                   # inflow from the neighbour
+                        Kn = nb[1] * n + nb[0]
+                        cols = slice((l * nx + Kn) * 4, (l * nx + Kn) * 4 + 4)
+                        L[rows, cols] += wl * on * nbrF[f]
+                    elif p.alpha is not None:              # inflow boundary: -int alpha Omega.nu v
+                        Q[rows] += -wl * on * _face_alpha_integrals(p.alpha[l], n, i, j, f, h)
+                qK = p.q[l, K] if p.q.ndim == 3 else p.q[K]
+                Q[rows] += wl * p.eps * (mass @ qK)
+    # S = M P: S[(l,p,r),(l',p,s)] = w_l w_l' int sigma_s/eps b_s b_r   (Appendix A)
+    for K in range(nx):
+        blk = (p.sigma_s[K] / p.eps) * mass
+        for l in range(na):
+            rows = slice((l * nx + K) * 4, (l * nx + K) * 4 + 4)
+            for m in range(na):
+                cols = slice((m * nx + K) * 4, (m * nx + K) * 4 + 4)
+                S[rows, cols] += p.w[l] * p.w[m] * blk
+    return L, S, Q
+
+
+def reconstruct(p, u0, alpha):
+    """Upwind reconstruction R_alpha Pi_0 (Section 3.3.1), 2D P1 slopes only.
+
+    ``u0``: cell averages ``[n_Omega][n_x]``.  Returns the Legendre coefficients ``[n_Omega][n_x][4]`` of
+    (delta_x u)(x - x_i) + (delta_y u)(y - y_j): coefficient of b1 = xi is (h/2) delta_x, of b2 = eta is
+    (h/2) delta_y.  delta uses the upwind side s_x = -sign(Omega_x); at the inflow boundary the difference is
+    taken with alpha at the face midpoint over a spacing h/2 (alpha None means 0).  The face-midpoint value
+    of the linear face data (a0 + a1 t) is a0.
+    """
+    n, h, na = p.n, p.h, p.nang
+    out = np.zeros((na, n * n, 4))
+    for l in range(na):
+        U = u0[l].reshape(n, n)              # [j][i]
+        dx = np.zeros((n, n))
+        dy = np.zeros((n, n))
+        if p.ox[l] > 0:                      # delta^-_x
+            dx[:, 1:] = (U[:, 1:] - U[:, :-1]) / h
+            aW = alpha[l, 0, :, 0] if alpha is not None else np.zeros(n)
+            dx[:, 0] = (U[:, 0] - aW) / (h / 2)
+        else:                                # delta^+_x
+            dx[:, :-1] = (U[:, 1:] - U[:, :-1]) / h
+            aE = alpha[l, 1, :, 0] if alpha is not None else np.zeros(n)
+            dx[:, -1] = (aE - U[:, -1]) / (h / 2)
+        if p.oy[l] > 0:
+            dy[1:, :] = (U[1:, :] - U[:-1, :]) / h
+            aS = alpha[l, 2, :, 0] if alpha is not None else np.zeros(n)
+            dy[0, :] = (U[0, :] - aS) / (h / 2)
+        else:
+            dy[:-1, :] = (U[1:, :] - U[:-1, :]) / h
+            aN = alpha[l, 3, :, 0] if alpha is not None else np.zeros(n)
+            dy[-1, :] = (aN - U[-1, :]) / (h / 2)
+        out[l, :, 1] = (h / 2) * dx.ravel()
+        out[l, :, 2] = (h / 2) * dy.ravel()
+    return out
+
+
+def _Rstar(p, u0, alpha):
+    """R*_alpha applied to the piecewise constants u0: R_alpha Pi_0 u minus its angular average."""
+    R = reconstruct(p, u0, alpha)
+    return R - np.einsum("l,lkr->kr", p.w, R)[None]
+
+
+def lm_basis(p):
+    """Basis matrix of V_h^lm: columns xi^{l,p,0} (l, p) then eta^{p,r} = sum_l xi^{l,p,r} (p, r = 1..3)."""
+    na, nx = p.nang, p.nx
+    dim = na * nx * 4
+    E = np.zeros((dim, na * nx + 3 * nx))
+    for l in range(na):
+        for K in range(nx):
+            E[(l * nx + K) * 4, l * nx + K] = 1.0
+    for K in range(nx):
+        for r in range(1, 4):
+            c = na * nx + K * 3 + (r - 1)
+            for l in range(na):
+                E[(l * nx + K) * 4 + r, c] = 1.0
+    return E
+
+
+def rlm_trial_basis(p):
+    """Trial basis of V_h^rlm: xi^{l,p,0} + R*_0 xi^{l,p,0}, then eta^{p,r} (Section 3.3.2)."""
+    na, nx = p.nang, p.nx
+    E = lm_basis(p)
+    Et = E.copy()
+    for l in range(na):
+        for K in range(nx):
+            u0 = np.zeros((na, nx))
+            u0[l, K] = 1.0
+            Rs = _Rstar(p, u0, None)
+            Et[:, l * nx + K] += Rs.ravel()
+    return Et
+
+
+def solve(p, variant):
+    """Solve the discrete problem.  Returns a dict with
+
+    ``psi``  full coefficients [n_Omega][n_x][4] of the (reconstructed) discrete solution,
+    ``phi``  scalar flux moments sum_l w_l psi_l, [n_x][4],
+    ``psi0``, ``phi1`` (low-memory variants) the V_h^lm coefficients: per-angle cell averages and the
+    isotropic slopes.
+    """
+    L, S, Q = assemble(p)
+    B = L - S
+    na, nx = p.nang, p.nx
+    out = {}
+    if variant == "std":
+        psi = np.linalg.solve(B, Q).reshape(na, nx, 4)
+    elif variant == "lm":
+        E = lm_basis(p)
+        c = np.linalg.solve(E.T @ B @ E, E.T @ Q)
+        psi = (E @ c).reshape(na, nx, 4)
+        out["psi0"] = c[:na * nx].reshape(na, nx)
+        out["phi1"] = c[na * nx:].reshape(nx, 3)
+    elif variant == "rlm":
+        E = lm_basis(p)
+        Et = rlm_trial_basis(p)
+        rho = _Rstar(p, np.zeros((na, nx)), p.alpha).ravel()   # affine part R*_alpha 0
+        c = np.linalg.solve(E.T @ B @ Et, E.T @ (Q - B @ rho))
+        psi = (Et @ c + rho).reshape(na, nx, 4)
+        out["psi0"] = c[:na * nx].reshape(na, nx)
+        out["phi1"] = c[na * nx:].reshape(nx, 3)
+    else:
+        raise ValueError(variant)
+    out["psi"] = psi
+    out["phi"] = np.einsum("l,lkr->kr", p.w, psi)
+    return out
+
+
+def operator_matrices(p):
+    """(L, S, Q) of Appendix A, exposed for adjoint and invariant checks."""
+    return assemble(p)
