@@ -1,0 +1,181 @@
+/* liblmdg -- low-memory discrete-ordinates discontinuous Galerkin transport sweeps on one GB300.
+ *
+ * C ABI for the hot path of Sun & Hauck, "Low-memory, discrete ordinates, discontinuous Galerkin methods
+ * for radiative transport" (arXiv 1907.01027): the upwind transport sweep of the standard Q1 S_N-DG scheme
+ * and of the two low-memory schemes, the angular reduction fused into the sweep, GMRES on the
+ * sweep-reduced systems, mixed-precision iterative refinement and the adjoint sweep.
+ *
+ * Problem (eq-main, Section 1): on a uniform n x n Cartesian mesh,
+ *   Omega . grad Psi + (sigma_s/eps + eps sigma_a) Psi = (sigma_s/eps) Psi_bar + eps q,  Psi = alpha on inflow,
+ * discretised by S_N collocation (eq:sn) and upwind DG with the Legendre Q1 basis (1, xi, eta, xi*eta) per
+ * cell (eq-Ljk, eq-sndg-scheme).
+ *
+ * Conventions for every entry point:
+ *   - Cell (i, j) (i along x, j along y) has index p = j*n + i.  Per-cell vectors are [n*n][4] doubles in the
+ *     Legendre basis above ("moments"), cell-major.
+ *   - Return value: 0 on success, a negative LMDG_ERR_* code otherwise; lmdg_strerror() describes it.
+ *   - Vectors passed to lmdg_sweep / lmdg_solve / lmdg_adjoint are DEVICE pointers (cudaMalloc'd memory of
+ *     the context's device) unless LMDG_HOST_PTRS is set in flags, in which case they are host pointers and
+ *     the call copies through its own device buffers.  The caller owns every buffer it passes.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls on a context are not thread safe;
+ *     use one context per host thread.  Device-pointer calls are asynchronous with respect to the host except
+ *     where stated; lmdg_solve and lmdg_adjoint synchronise the stream (they read residual norms).
+ *   - No entry point throws; CUDA failures are reported as LMDG_ERR_CUDA.
+ */
+#ifndef LMDG_H
+#define LMDG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lmdg_ctx lmdg_ctx;
+
+/* Scheme: standard S_N-DG with the full Q1 space V_h (eq-sndg-scheme); low-memory LMDG with
+ * V_h^lm = V_{h,0} + D_{h,1} (eq-gene-scheme, Section 3.2); reconstructed RLMDG (eq-rlmdg-vari,
+ * Section 3.3). */
+enum { LMDG_STD = 0, LMDG_LM = 1, LMDG_RLM = 2 };
+
+/* Arithmetic of the sweeps inside lmdg_solve.  FP64: everything in double.  FP32: sweeps in float inside an
+ * FP64 iterative-refinement loop (residuals, GMRES orthogonalisation and least squares stay FP64).
+ * FP32_BF16STORE: as FP32, and the angular unknowns written by storing sweeps are bfloat16. */
+enum { LMDG_FP64 = 0, LMDG_FP32 = 1, LMDG_FP32_BF16STORE = 2 };
+
+/* lmdg_sweep flags */
+enum {
+  LMDG_SWEEP_SOURCE = 1,   /* y = K x - b (affine map whose zero solves the reduced system) instead of y = K x */
+  LMDG_SWEEP_FP32 = 2,     /* run the sweep in float (x, y stay double) */
+  LMDG_SWEEP_STORE = 4,    /* also store the angular unknowns of this sweep in the context (see lmdg_get_psi) */
+  LMDG_HOST_PTRS = 8       /* x, y (and other vectors of the call) are host pointers */
+};
+
+/* Errors */
+enum {
+  LMDG_OK = 0,
+  LMDG_ERR_ARG = -1,        /* invalid argument (sizes, NULL, eps <= 0, negative cross sections, ...) */
+  LMDG_ERR_QUAD = -2,       /* quadrature: sum w != 1, a direction on an axis, or n_Omega not 4 * k */
+  LMDG_ERR_NOMEM = -3,      /* device allocation failed */
+  LMDG_ERR_CUDA = -4,       /* a CUDA call failed */
+  LMDG_ERR_NOTCONV = -5,    /* iteration limit reached before the tolerance (the output still holds the
+                               last iterate) */
+  LMDG_ERR_TIMEOUT = -6,    /* a sweep kernel gave up waiting for an upstream tile (spin limit); the
+                               kernel exits cleanly and the context stays usable */
+  LMDG_ERR_BREAKDOWN = -7,  /* non-finite residual or Krylov breakdown */
+  LMDG_ERR_STATE = -8       /* call out of order (e.g. lmdg_get_psi before a storing sweep) */
+};
+
+typedef struct {
+  int n;               /* cells per side (n >= 1) */
+  double x0, y0;       /* lower-left corner */
+  double h;            /* cell side (> 0) */
+} lmdg_mesh;
+
+typedef struct {
+  int n;               /* number of directions n_Omega: a multiple of 4, at most 1024 */
+  const double *ox;    /* host [n] Omega_x, none zero, |Omega| < 1 (projection of the unit sphere) */
+  const double *oy;    /* host [n] Omega_y, none zero */
+  const double *w;     /* host [n] positive weights summing to 1 (eq-polyquad (i)) */
+} lmdg_quadrature;
+
+typedef struct {
+  int precision;       /* LMDG_FP64 (default), LMDG_FP32 or LMDG_FP32_BF16STORE: sweeps inside lmdg_solve */
+  int restart;         /* GMRES restart length m (default 30, at most 120) */
+  int max_iters;       /* cap on the total number of GMRES iterations (default 5000) */
+  double tol;          /* relative residual target ||r_k|| <= tol ||r_0|| (default 1e-8) */
+  double inner_tol;    /* FP32 modes: relative tolerance of each inner GMRES solve (default 1e-4) */
+  int max_refine;      /* FP32 modes: cap on outer refinement steps (default 50) */
+  int precond;         /* 1 (default): right preconditioner diag(I, diag(B11))^-1 for LMDG/RLMDG; 0: none */
+  long long spin_limit;/* polls of a readiness flag before a sweep reports LMDG_ERR_TIMEOUT (default 2^26) */
+  int device;          /* CUDA device ordinal (default 0) */
+} lmdg_options;
+
+typedef struct {
+  int iters;           /* GMRES iterations (all restarts, all refinement steps) */
+  int refinements;     /* outer FP64 refinement steps (FP32 modes), 0 for FP64 */
+  int sweeps_fp64;     /* full transport sweeps run in FP64 */
+  int sweeps_fp32;     /* full transport sweeps run in FP32 */
+  double resid0;       /* ||r_0|| */
+  double resid;        /* final ||b - K x|| from an FP64 sweep */
+  double time_ms;      /* wall time of the call (host clock) */
+  double sweep_ms;     /* device time spent in sweep kernels (CUDA events) */
+} lmdg_stats;
+
+/* Fill *opt with the defaults listed above. */
+int lmdg_default_options(lmdg_options *opt);
+
+/* Create a problem context (setup step: Section 2.1 data).  All inputs are host pointers and are copied.
+ *   sigma_s, sigma_a : [n*n] per-cell cross sections, sigma_s >= 0, sigma_a >= 0, sigma_t > 0 everywhere.
+ *   q                : source as Legendre moments; q_layout 0: [n*n] cell constants; 1: [n*n][4];
+ *                      2: [n_Omega][n*n][4] angle dependent (Section 4.1 allows q to depend on angle).
+ *   alpha            : inflow data, NULL for vacuum; otherwise [n_Omega][4][n][2]: per direction, side
+ *                      (0 west x = x0, 1 east, 2 south y = y0, 3 north) and boundary face, the coefficients
+ *                      (a0, a1) of alpha = a0 + a1 t along the face, t in [-1, 1] increasing with the global
+ *                      coordinate.  Only inflow faces are read.  The reconstruction of RLMDG uses a0 as the
+ *                      face-midpoint value of alpha (Section 3.3.1).
+ *   eps              : scaling parameter epsilon > 0 of eq-main.
+ *   variant          : LMDG_STD, LMDG_LM or LMDG_RLM.
+ *   opt              : NULL for defaults.
+ * Device memory: O(n_Omega * n^2) for the angular-flux store, O(n^2) for the rest. */
+int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad,
+               const double *sigma_s, const double *sigma_a, const double *q, int q_layout,
+               const double *alpha, double eps, int variant, const lmdg_options *opt);
+
+/* One application of the sweep-reduced operator (one transport sweep over all directions with the angular
+ * reduction fused into it), on vectors of [n*n][4] doubles:
+ *   LMDG_STD : K x = x - P L^-1 M x  (eq-sndg-phi), x = Phi, the scalar-flux moments;
+ *              b = P L^-1 Q.
+ *   LMDG_LM  : K [X0; X1] of eq-lmdg-reducemat, evaluated as in eq-nonrec-block; x = (X0, X1) per cell;
+ *              b = the right-hand side of eq-lmdg-reducemat minus K [0; z], z = B11^-1 Sigma Q1.
+ *   LMDG_RLM : the reduced RLMDG operator of Section 3.3.2 with the second block row
+ *              G' = Sigma Ltilde10 + B11 P1 R (the printed row does not close; see the design notes);
+ *              b = its right-hand side minus K [0; z], z = B11^-1 Sigma Qtilde1.
+ * With LMDG_SWEEP_SOURCE the call returns y = K x - b, so that the solution of lmdg_solve zeroes it (for the
+ * low-memory variants this is the paper's system written for the shifted unknown X1 - z, i.e. GMRES started
+ * from X1 = z).  LMDG_SWEEP_STORE keeps this sweep's angular unknowns: psi [n_Omega][n*n][4] for LMDG_STD,
+ * psi0 [n_Omega][n*n] for the low-memory variants.  Asynchronous on stream for device pointers. */
+int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
+
+/* Solve the reduced system with restarted GMRES (right-preconditioned, see lmdg_options.precond), then run
+ * the recovery sweep (eq-sndg-final-sweep, eq-lm-step4 and its RLMDG analogue), storing the angular unknowns.
+ *   x0  : initial guess [n*n][4] (NULL = zero), in the unknowns of lmdg_sweep with LMDG_SWEEP_SOURCE.
+ *   x   : output [n*n][4], the converged unknowns (may be NULL).
+ *   phi : output [n*n][4], the scalar-flux moments sum_l w_l psi_l of the discrete solution (may be NULL).
+ *   stats: may be NULL.
+ * Returns LMDG_ERR_NOTCONV (with outputs written) if max_iters is reached. */
+int lmdg_solve(lmdg_ctx *ctx, const double *x0, double *x, double *phi, lmdg_stats *stats, int flags,
+               void *stream);
+
+/* Copy the angular unknowns kept by the last storing sweep (lmdg_solve always stores) to psi:
+ * LMDG_STD [n_Omega][n*n][4], low-memory variants [n_Omega][n*n] (cell averages psi0; the isotropic slopes
+ * are the phi output of lmdg_solve).  Directions in the order given to lmdg_setup. */
+int lmdg_get_psi(lmdg_ctx *ctx, double *psi, int flags, void *stream);
+
+/* Adjoint sensitivities of the detector functional J = sum_K g_K int_K Psi_bar dx (g: [n*n] weights) with
+ * respect to the per-cell sigma_s, sigma_a and the per-cell constant source q (LMDG_STD).  Solves the
+ * transposed reduced system with reverse-order transposed sweeps and combines forward and adjoint angular
+ * fluxes cell by cell.  Outputs [n*n] each (any may be NULL) and J. */
+int lmdg_adjoint(lmdg_ctx *ctx, const double *g, double *dJ_dsigma_s, double *dJ_dsigma_a,
+                 double *dJ_dq, double *J, lmdg_stats *stats, int flags, void *stream);
+
+/* B11 = Sigma L11 Sigma^T - Sigma M1 of eq-lmdg-psi1 (the isotropic-slope block) applied to x [n*n][3]:
+ * y [n*n][3].  Provided for the paper-literal reduced right-hand side and for checking. */
+int lmdg_b11_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
+
+/* Solve B11 z = r by conjugate gradients (B11 is SPD for centrally symmetric quadratures, Theorem
+ * lem-B11) to relative residual tol; iters (may be NULL) receives the iteration count. */
+int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *iters, int flags,
+                   void *stream);
+
+/* Problem sizes of a context: n, n_Omega, variant. */
+int lmdg_info(const lmdg_ctx *ctx, int *n, int *n_omega, int *variant);
+
+/* Free every device buffer of the context.  NULL is ignored. */
+void lmdg_destroy(lmdg_ctx *ctx);
+
+/* Static description of an error code. */
+const char *lmdg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMDG_H */

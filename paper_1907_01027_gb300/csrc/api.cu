@@ -1,0 +1,657 @@
+// C ABI of liblmdg: problem setup, sweeps, GMRES solve with FP64 or mixed-precision iterative refinement,
+// B11 apply/CG, and the angular-flux store.  See include/lmdg.h for the contract of every entry point.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lmdg_internal.h"
+#include "krylov.h"
+
+using namespace lmdg;
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return LMDG_ERR_CUDA;   \
+  } while (0)
+
+int quadrant(double ox, double oy) { return oy > 0 ? (ox > 0 ? 0 : 1) : (ox < 0 ? 2 : 3); }
+
+template <typename T>
+int upload(T **dst, const std::vector<double> &src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, tmp.size())) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (!tmp.empty()) CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+template <typename T>
+void free_pd(ProblemData<T> &p) {
+  cudaFree(p.ox); cudaFree(p.oy); cudaFree(p.w); cudaFree(p.sigt); cudaFree(p.sse); cudaFree(p.q);
+  cudaFree(p.alpha);
+  p = ProblemData<T>();
+}
+
+// Launch geometry: enough (quadrant, group, strip) CTAs to cover ~2 per SM, at most 8 warps per CTA and
+// kMaxA directions per warp.  LMDG_SWEEP_GEOM="groups,warps,apw" overrides it (tuning only).
+SweepGeom choose_geom(int n, int nq, int nsm, bool fp64) {
+  SweepGeom g;
+  g.strips = (n + 31) / 32;
+  int target = 2 * nsm;
+  int G = std::max(1, std::min(nq, (target + 4 * g.strips - 1) / (4 * g.strips)));
+  int gsize = (nq + G - 1) / G;
+  int apw = std::max(1, std::min(kMaxA, (gsize + 7) / 8));
+  if (fp64 && gsize >= 4 && apw < 2) apw = 2;
+  int W = (gsize + apw - 1) / apw;
+  g.groups = G; g.warps = W; g.apw = apw;
+  if (const char *e = std::getenv("LMDG_SWEEP_GEOM")) {
+    int a = 0, b = 0, c = 0;
+    if (std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a >= 1 && a <= nq && c >= 1 && c <= kMaxA && b >= 1 &&
+        b <= 8) {
+      int gs = (nq + a - 1) / a;
+      if (b * c >= gs && b <= gs) { g.groups = a; g.warps = b; g.apw = c; }
+    }
+  }
+  // every group must be non-empty and every warp must own at least one direction
+  while (g.groups > 1 && (g.groups - 1) * ((nq + g.groups - 1) / g.groups) >= nq) --g.groups;
+  gsize = (nq + g.groups - 1) / g.groups;
+  int last = nq - (g.groups - 1) * gsize;
+  if (g.warps > last) g.warps = last;
+  g.apw = (gsize + g.warps - 1) / g.warps;
+  if (g.apw > kMaxA) { g.apw = kMaxA; g.warps = (gsize + kMaxA - 1) / kMaxA; }
+  return g;
+}
+
+size_t part_elems(const SweepGeom &g, int nx) { return (size_t)4 * g.groups * nx * 6; }
+
+template <typename T>
+int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s) {
+  SweepArgs<T> a{};
+  const bool f64 = sizeof(T) == 8;
+  a.n = c->n; a.nq = c->nq; a.nang = c->nang; a.nx = c->nx;
+  a.h = (T)c->h; a.eps = (T)c->eps;
+  a.g = f64 ? c->g64 : c->g32;
+  if constexpr (sizeof(T) == 8) { a.pd = c->d64; a.p1ra = c->p1ra64; }
+  else { a.pd = c->d32; a.p1ra = c->p1ra32; }
+  a.q_per_angle = c->q_layout == 2;
+  a.X = X;
+  a.source = source;
+  a.part = reinterpret_cast<T *>(c->part);
+  a.perm = c->perm;
+  a.ytr = reinterpret_cast<T *>(c->ytr);
+  a.ctrl = c->ctrl;
+  a.spin_limit = c->opt.spin_limit;
+  a.psi = nullptr;
+  a.psi_bf16 = 0;
+  if (store) {
+    int kind = f64 ? 0 : (bf16 && c->variant != LMDG_STD ? 2 : 1);
+    size_t per = c->variant == LMDG_STD ? 4 : 1;
+    size_t elems = (size_t)c->nang * c->nx * per;
+    size_t bytes = elems * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
+    if (c->psi == nullptr) {
+      // sized for the widest kind so any precision can reuse the buffer
+      if (cudaMalloc(&c->psi, elems * 8) != cudaSuccess) return LMDG_ERR_NOMEM;
+    }
+    (void)bytes;
+    c->psi_kind = kind;
+    c->psi_elems = elems;
+    a.psi = c->psi;
+    a.psi_bf16 = kind == 2;
+  }
+  const bool timed = c->ev0 != nullptr;
+  if (timed) CK(cudaEventRecord(c->ev0, s));
+  CK(launch_sweep<T>(c->variant, a, s));
+  if (timed) CK(cudaEventRecord(c->ev1, s));
+  CK(launch_epilogue<T>(c->variant, c->n, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->p1ra64,
+                        c->sq1, source, y, s));
+  if (f64) c->sweeps64++; else c->sweeps32++;
+  return 0;
+}
+
+int sweep_prec(lmdg_ctx *c, int fp32, const double *X, double *y, int source, bool store, int bf16,
+               cudaStream_t s) {
+  return fp32 ? do_sweep<float>(c, X, y, source, store, bf16, s) : do_sweep<double>(c, X, y, source, store, 0, s);
+}
+
+int check_error_word(lmdg_ctx *c, cudaStream_t s) {
+  unsigned err = 0;
+  CK(cudaMemcpyAsync(&err, c->ctrl + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return err ? LMDG_ERR_TIMEOUT : 0;
+}
+
+// phi = scalar-flux moments from the partial reductions of the last sweep at X (low-memory variants):
+// phi0 = P0 psi0, phi_r = -W_r + (P1 R psi0)_r (RLMDG, alpha part removed), W = X1 - z the GMRES unknown.
+template <typename T, int VAR>
+__global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const double *__restrict__ X,
+                           const double *__restrict__ p1ra, double *__restrict__ phi) {
+  constexpr int NR = (VAR == 2) ? 6 : 4;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  double s[NR];
+  for (int r = 0; r < NR; ++r) s[r] = 0;
+  for (int p = 0; p < P; ++p)
+    for (int r = 0; r < NR; ++r) s[r] += (double)part[((size_t)p * nx + K) * NR + r];
+  const double *x = X + 4 * (size_t)K;
+  double *o = phi + 4 * (size_t)K;
+  o[0] = s[0];
+  o[1] = -x[1]; o[2] = -x[2]; o[3] = -x[3];
+  if (VAR == 2) {
+    o[1] += s[4] - (p1ra ? p1ra[2 * (size_t)K] : 0.0);
+    o[2] += s[5] - (p1ra ? p1ra[2 * (size_t)K + 1] : 0.0);
+  }
+}
+
+int ensure_krylov(lmdg_ctx *c, int m) {
+  const size_t N = 4 * (size_t)c->nx;
+  if (c->V && c->red_len >= m + 2) return 0;
+  cudaFree(c->V);
+  for (auto &v : c->vec) { cudaFree(v); v = nullptr; }
+  cudaFree(c->red);
+  if (c->red_h) cudaFreeHost(c->red_h);
+  c->V = nullptr; c->red = nullptr; c->red_h = nullptr;
+  if (cudaMalloc(&c->V, sizeof(double) * N * (m + 1)) != cudaSuccess) return LMDG_ERR_NOMEM;
+  for (auto &v : c->vec)
+    if (cudaMalloc(&v, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+  size_t rl = mdot_partial_len(m + 2) + 4 * (size_t)(m + 2);
+  if (cudaMalloc(&c->red, sizeof(double) * rl) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (cudaMallocHost(&c->red_h, sizeof(double) * 4 * (m + 2)) != cudaSuccess) return LMDG_ERR_NOMEM;
+  c->red_len = m + 2;
+  return 0;
+}
+
+// ||v||^2 into *out_h (synchronises)
+int norm2(lmdg_ctx *c, const double *v, double *out_h, cudaStream_t s) {
+  const size_t N = 4 * (size_t)c->nx;
+  double *partial = c->red, *out = c->red + mdot_partial_len(c->red_len);
+  CK(mdot(v, N, 1, v, N, partial, out, 0, s));
+  CK(cudaMemcpyAsync(out_h, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+struct GmresOut {
+  int iters = 0;
+  double est = 0;
+  bool breakdown = false;
+};
+
+// One GMRES(m) cycle from a zero initial guess for K d = r, ||r|| = rnorm: d (device) receives the
+// correction Minv V y.  Stops early when the least-squares residual reaches target.
+int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d, int m, double target,
+                int max_it, GmresOut *go, cudaStream_t s) {
+  const size_t N = 4 * (size_t)c->nx;
+  double *V = c->V;
+  double *z = c->vec[0], *w = c->vec[1];
+  double *partial = c->red;
+  double *hdev = c->red + mdot_partial_len(c->red_len);          // [m+2]
+  double *h2dev = hdev + (m + 2);
+  double *ydev = h2dev + (m + 2);
+  const int pmode = (c->variant != LMDG_STD && c->opt.precond) ? 1 : 0;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+  g[0] = rnorm;
+  CK(axpby(V, 1.0 / rnorm, r, 0.0, N, s));
+  int k = 0;
+  go->breakdown = false;
+  for (int j = 0; j < m && j < max_it; ++j) {
+    double *vj = V + (size_t)j * N;
+    CK(precond(z, vj, c->b11diag, c->nx, pmode, s));
+    if (int e = sweep_prec(c, fp32, z, w, 0, false, 0, s)) return e;
+    // classical Gram-Schmidt, twice
+    CK(mdot(V, N, j + 1, w, N, partial, hdev, 0, s));
+    CK(maxpy(w, V, N, j + 1, hdev, N, s));
+    CK(mdot(V, N, j + 1, w, N, partial, h2dev, 0, s));
+    CK(maxpy(w, V, N, j + 1, h2dev, N, s));
+    CK(mdot(w, N, 1, w, N, partial, h2dev + j + 1, 0, s));
+    CK(cudaMemcpyAsync(c->red_h, hdev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->red_h + (m + 2), h2dev, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    if (int e = check_error_word(c, s)) return e;   // synchronises
+    double *col = &H[(size_t)j * (m + 1)];
+    for (int i = 0; i <= j; ++i) col[i] = c->red_h[i] + c->red_h[m + 2 + i];
+    const double hn = std::sqrt(std::max(0.0, c->red_h[m + 2 + j + 1]));
+    col[j + 1] = hn;
+    if (!std::isfinite(hn)) return LMDG_ERR_BREAKDOWN;
+    const bool invariant = hn <= 1e-14 * std::fabs(rnorm) || hn == 0.0;
+    if (!invariant) CK(scale_by_inv(V + (size_t)(j + 1) * N, w, h2dev + j + 1, N, s));
+    for (int i = 0; i < j; ++i) {
+      const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t0;
+    }
+    const double den = std::hypot(col[j], col[j + 1]);
+    cs[j] = den == 0 ? 1.0 : col[j] / den;
+    sn[j] = den == 0 ? 0.0 : col[j + 1] / den;
+    col[j] = den;
+    col[j + 1] = 0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    k = j + 1;
+    go->est = std::fabs(g[j + 1]);
+    if (go->est <= target || invariant) { go->breakdown = invariant; break; }
+  }
+  // back substitution H y = g
+  std::vector<double> yv(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double sacc = g[i];
+    for (int l = i + 1; l < k; ++l) sacc -= H[(size_t)l * (m + 1) + i] * yv[l];
+    yv[i] = sacc / H[(size_t)i * (m + 1) + i];
+  }
+  for (int i = 0; i < k; ++i) c->red_h[i] = -yv[i];
+  CK(cudaMemcpyAsync(ydev, c->red_h, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
+  CK(maxpy(z, V, N, k, ydev, N, s));
+  CK(precond(d, z, c->b11diag, c->nx, pmode, s));
+  CK(cudaStreamSynchronize(s));
+  go->iters = k;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lmdg_default_options(lmdg_options *o) {
+  if (!o) return LMDG_ERR_ARG;
+  o->precision = LMDG_FP64;
+  o->restart = 30;
+  o->max_iters = 5000;
+  o->tol = 1e-8;
+  o->inner_tol = 1e-4;
+  o->max_refine = 50;
+  o->precond = 1;
+  o->spin_limit = 1LL << 26;
+  o->device = 0;
+  return 0;
+}
+
+const char *lmdg_strerror(int code) {
+  switch (code) {
+    case LMDG_OK: return "success";
+    case LMDG_ERR_ARG: return "invalid argument";
+    case LMDG_ERR_QUAD: return "invalid quadrature (weights must be positive and sum to 1, no direction on an "
+                               "axis, equal number of directions per quadrant)";
+    case LMDG_ERR_NOMEM: return "device allocation failed";
+    case LMDG_ERR_CUDA: return "CUDA call failed";
+    case LMDG_ERR_NOTCONV: return "iteration limit reached before the tolerance";
+    case LMDG_ERR_TIMEOUT: return "sweep gave up waiting for an upstream strip (spin limit)";
+    case LMDG_ERR_BREAKDOWN: return "non-finite residual or Krylov breakdown";
+    case LMDG_ERR_STATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+int lmdg_info(const lmdg_ctx *c, int *n, int *nang, int *variant) {
+  if (!c) return LMDG_ERR_ARG;
+  if (n) *n = c->n;
+  if (nang) *nang = c->nang;
+  if (variant) *variant = c->variant;
+  return 0;
+}
+
+void lmdg_destroy(lmdg_ctx *c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->dev);
+  free_pd(c->d64);
+  free_pd(c->d32);
+  cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11diag);
+  cudaFree(c->sigma_a); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
+  cudaFree(c->V);
+  for (auto &v : c->vec) cudaFree(v);
+  cudaFree(c->red);
+  if (c->red_h) cudaFreeHost(c->red_h);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete[] c->perm_h;
+  delete c;
+  cudaSetDevice(prev);
+}
+
+int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad, const double *sigma_s,
+               const double *sigma_a, const double *q, int q_layout, const double *alpha, double eps,
+               int variant, const lmdg_options *opt) {
+  if (!out || !mesh || !quad || !sigma_s || !sigma_a || !q) return LMDG_ERR_ARG;
+  *out = nullptr;
+  const int n = mesh->n;
+  if (n < 1 || n > 65536 || !(mesh->h > 0) || !std::isfinite(mesh->h)) return LMDG_ERR_ARG;
+  if (!(eps > 1e-12) || !std::isfinite(eps)) return LMDG_ERR_ARG;
+  if (variant < LMDG_STD || variant > LMDG_RLM || q_layout < 0 || q_layout > 2) return LMDG_ERR_ARG;
+  const int na = quad->n;
+  if (na < 4 || na > 1024 || na % 4 || !quad->ox || !quad->oy || !quad->w) return LMDG_ERR_QUAD;
+  double wsum = 0;
+  int cnt[4] = {0, 0, 0, 0};
+  for (int l = 0; l < na; ++l) {
+    const double a = quad->ox[l], b = quad->oy[l], w = quad->w[l];
+    if (!(w > 0) || a == 0 || b == 0 || !std::isfinite(a) || !std::isfinite(b) || a * a + b * b > 1.0 + 1e-12)
+      return LMDG_ERR_QUAD;
+    wsum += w;
+    cnt[quadrant(a, b)]++;
+  }
+  if (std::fabs(wsum - 1.0) > 1e-12) return LMDG_ERR_QUAD;
+  if (cnt[0] != na / 4 || cnt[1] != na / 4 || cnt[2] != na / 4 || cnt[3] != na / 4) return LMDG_ERR_QUAD;
+  const size_t nx = (size_t)n * n;
+  for (size_t K = 0; K < nx; ++K) {
+    const double ss = sigma_s[K], sa = sigma_a[K];
+    if (!(ss >= 0) || !(sa >= 0) || !std::isfinite(ss) || !std::isfinite(sa) || !(ss / eps + eps * sa > 0))
+      return LMDG_ERR_ARG;
+  }
+  lmdg_options o;
+  lmdg_default_options(&o);
+  if (opt) o = *opt;
+  if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1)
+    return LMDG_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
+  CK(cudaSetDevice(o.device));
+
+  lmdg_ctx *c = new (std::nothrow) lmdg_ctx();
+  if (!c) return LMDG_ERR_NOMEM;
+  c->n = n; c->nx = (int)nx; c->nang = na; c->nq = na / 4; c->variant = variant; c->q_layout = q_layout;
+  c->has_alpha = alpha != nullptr; c->dev = o.device; c->h = mesh->h; c->eps = eps;
+  c->x0 = mesh->x0; c->y0 = mesh->y0; c->opt = o;
+  auto fail = [&](int e) { lmdg_destroy(c); return e; };
+
+  // directions sorted by quadrant, stable within a quadrant
+  std::vector<int> perm(na);
+  for (int l = 0; l < na; ++l) perm[l] = l;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    return quadrant(quad->ox[a], quad->oy[a]) < quadrant(quad->ox[b], quad->oy[b]);
+  });
+  c->perm_h = new int[na];
+  std::copy(perm.begin(), perm.end(), c->perm_h);
+  std::vector<double> ox(na), oy(na), w(na);
+  for (int k = 0; k < na; ++k) { ox[k] = quad->ox[perm[k]]; oy[k] = quad->oy[perm[k]]; w[k] = quad->w[perm[k]]; }
+  std::vector<double> sigt(nx), sse(nx), sa(sigma_a, sigma_a + nx);
+  for (size_t K = 0; K < nx; ++K) { sigt[K] = sigma_s[K] / eps + eps * sigma_a[K]; sse[K] = sigma_s[K] / eps; }
+  std::vector<double> qv;
+  if (q_layout == 0) {
+    qv.assign(nx * 4, 0.0);
+    for (size_t K = 0; K < nx; ++K) qv[4 * K] = q[K];
+  } else if (q_layout == 1) {
+    qv.assign(q, q + nx * 4);
+  } else {
+    qv.resize((size_t)na * nx * 4);
+    for (int k = 0; k < na; ++k)
+      std::memcpy(&qv[(size_t)k * nx * 4], q + (size_t)perm[k] * nx * 4, sizeof(double) * nx * 4);
+  }
+  std::vector<double> av;
+  if (alpha) {
+    const size_t per = (size_t)4 * n * 2;
+    av.resize((size_t)na * per);
+    for (int k = 0; k < na; ++k) std::memcpy(&av[(size_t)k * per], alpha + (size_t)perm[k] * per, sizeof(double) * per);
+  }
+
+  // Sigma Q1 = sum_l w_l (eps int q_l b_r + inflow-boundary terms), r = 1..3 (low-memory right-hand sides)
+  // P1 r_alpha = angular average of the boundary part of the reconstruction (RLMDG)
+  std::vector<double> sq1(nx * 3, 0.0), p1ra(nx * 2, 0.0);
+  const double h = mesh->h;
+  const double D[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
+  for (size_t K = 0; K < nx; ++K)
+    for (int r = 0; r < 3; ++r) {
+      double qs = 0;
+      if (q_layout == 1) qs = q[4 * K + 1 + r];
+      else if (q_layout == 2)
+        for (int l = 0; l < na; ++l) qs += quad->w[l] * q[((size_t)l * nx + K) * 4 + 1 + r];
+      sq1[3 * K + r] = eps * h * h * D[r] * qs;
+    }
+  double Ax[2] = {0, 0}, Ay[2] = {0, 0};
+  for (int l = 0; l < na; ++l) {
+    const double a = quad->ox[l], b = quad->oy[l], wl = quad->w[l];
+    Ax[a > 0 ? 0 : 1] += wl * std::fabs(a);
+    Ay[b > 0 ? 0 : 1] += wl * std::fabs(b);
+    if (!alpha) continue;
+    const double sx = a > 0 ? 1 : -1, sy = b > 0 ? 1 : -1, aa = std::fabs(a), bb = std::fabs(b);
+    const double *al = alpha + (size_t)l * 4 * n * 2;
+    const int i0 = a > 0 ? 0 : n - 1, sidex = a > 0 ? 0 : 1;
+    for (int j = 0; j < n; ++j) {
+      const size_t K = (size_t)j * n + i0;
+      const double a0 = al[((size_t)sidex * n + j) * 2], a1 = al[((size_t)sidex * n + j) * 2 + 1];
+      sq1[3 * K + 0] += wl * (-sx * aa * h * a0);
+      sq1[3 * K + 1] += wl * (aa * h / 3.0 * a1);
+      sq1[3 * K + 2] += wl * (-sx * aa * h / 3.0 * a1);
+      p1ra[2 * K + 0] += wl * sx * (-a0);
+    }
+    const int j0 = b > 0 ? 0 : n - 1, sidey = b > 0 ? 2 : 3;
+    for (int i = 0; i < n; ++i) {
+      const size_t K = (size_t)j0 * n + i;
+      const double a0 = al[((size_t)sidey * n + i) * 2], a1 = al[((size_t)sidey * n + i) * 2 + 1];
+      sq1[3 * K + 0] += wl * (bb * h / 3.0 * a1);
+      sq1[3 * K + 1] += wl * (-sy * bb * h * a0);
+      sq1[3 * K + 2] += wl * (-sy * bb * h / 3.0 * a1);
+      p1ra[2 * K + 1] += wl * sy * (-a0);
+    }
+  }
+  c->Ax[0] = Ax[0]; c->Ax[1] = Ax[1]; c->Ay[0] = Ay[0]; c->Ay[1] = Ay[1];
+  // diagonal of B11: eps sigma_a h^2 D_r + outflow face terms (Jacobi right preconditioner)
+  std::vector<double> bd(nx * 3);
+  const double fx[3] = {1.0, 1.0 / 3.0, 1.0 / 3.0}, fy[3] = {1.0 / 3.0, 1.0, 1.0 / 3.0};
+  for (size_t K = 0; K < nx; ++K)
+    for (int r = 0; r < 3; ++r)
+      bd[3 * K + r] = eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r];
+
+  int e = 0;
+  std::vector<double> permd(perm.begin(), perm.end());
+  if (cudaMalloc(&c->perm, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (cudaMemcpy(c->perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LMDG_ERR_CUDA);
+  if ((e = upload(&c->d64.ox, ox)) || (e = upload(&c->d64.oy, oy)) || (e = upload(&c->d64.w, w)) ||
+      (e = upload(&c->d64.sigt, sigt)) || (e = upload(&c->d64.sse, sse)) || (e = upload(&c->d64.q, qv)) ||
+      (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
+      (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qv)) ||
+      (e = upload(&c->p1ra64, p1ra)) || (e = upload(&c->p1ra32, p1ra)) || (e = upload(&c->sq1, sq1)) ||
+      (e = upload(&c->b11diag, bd)) || (e = upload(&c->sigma_a, sa)))
+    return fail(e);
+  if (alpha) {
+    if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, o.device);
+  c->g64 = choose_geom(n, c->nq, nsm, true);
+  c->g32 = choose_geom(n, c->nq, nsm, false);
+  const size_t pe = std::max(part_elems(c->g64, c->nx), part_elems(c->g32, c->nx));
+  if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  const int strips = (n + 31) / 32;
+  if (cudaMalloc(&c->ytr, sizeof(double) * (size_t)na * strips * n * 3) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  c->ctrl_words = 2 + (size_t)std::max(c->g64.units(), c->g32.units());
+  if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);
+  *out = c;
+  return 0;
+}
+
+int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream) {
+  if (!c || !x || !y) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const size_t N = 4 * (size_t)c->nx;
+  const double *xd = x;
+  double *yd = y;
+  if (flags & LMDG_HOST_PTRS) {
+    if (int e = ensure_krylov(c, c->opt.restart)) return e;
+    CK(cudaMemcpyAsync(c->vec[4], x, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    xd = c->vec[4];
+    yd = c->vec[5];
+  }
+  if (int e = sweep_prec(c, (flags & LMDG_SWEEP_FP32) ? 1 : 0, xd, yd, (flags & LMDG_SWEEP_SOURCE) ? 1 : 0,
+                         (flags & LMDG_SWEEP_STORE) != 0, 0, s))
+    return e;
+  if (flags & LMDG_HOST_PTRS) CK(cudaMemcpyAsync(y, yd, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  return check_error_word(c, s);
+}
+
+int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
+  if (!c || !psi) return LMDG_ERR_ARG;
+  if (c->psi_kind < 0) return LMDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  if (flags & LMDG_HOST_PTRS) {
+    double *tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
+    cudaError_t e1 = lmdg::to_double(tmp, c->psi, c->psi_kind, c->psi_elems, s);
+    cudaError_t e2 = cudaMemcpyAsync(psi, tmp, sizeof(double) * c->psi_elems, cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    return (e1 || e2 || e3) ? LMDG_ERR_CUDA : 0;
+  }
+  CK(lmdg::to_double(psi, c->psi, c->psi_kind, c->psi_elems, s));
+  return 0;
+}
+
+int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats *st, int flags, void *stream) {
+  if (!c) return LMDG_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const int m = c->opt.restart;
+  if (int e = ensure_krylov(c, m)) return e;
+  const size_t N = 4 * (size_t)c->nx;
+  const int fp32 = c->opt.precision != LMDG_FP64;
+  const int bf16 = c->opt.precision == LMDG_FP32_BF16STORE;
+  double *X = c->vec[2], *R = c->vec[3], *D = c->vec[4];
+  c->sweeps64 = c->sweeps32 = 0;
+  if (!c->ev0) { CK(cudaEventCreate(&c->ev0)); CK(cudaEventCreate(&c->ev1)); }
+  c->sweep_ms_acc = 0;
+  if (x0) CK(cudaMemcpyAsync(X, x0, sizeof(double) * N,
+                             (flags & LMDG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(X, 0, sizeof(double) * N, s));
+  // r = -(K x - b), FP64, storing (the last one is the recovery sweep in FP64 mode)
+  auto residual = [&](double *rn2) -> int {
+    if (int e = sweep_prec(c, 0, X, R, 1, !fp32, 0, s)) return e;
+    CK(axpby(R, -1.0, R, 0.0, N, s));
+    if (int e = check_error_word(c, s)) return e;
+    return norm2(c, R, rn2, s);
+  };
+  double rn2 = 0;
+  if (int e = residual(&rn2)) return e;
+  const double r0 = std::sqrt(rn2);
+  if (!std::isfinite(r0)) return LMDG_ERR_BREAKDOWN;
+  double rn = r0;
+  int iters = 0, refine = 0, status = 0;
+  while (rn > c->opt.tol * r0) {
+    if (iters >= c->opt.max_iters || (fp32 && refine >= c->opt.max_refine)) { status = LMDG_ERR_NOTCONV; break; }
+    const double target = fp32 ? std::max(c->opt.inner_tol * rn, 0.5 * c->opt.tol * r0) : c->opt.tol * r0;
+    GmresOut go;
+    if (int e = gmres_cycle(c, fp32, R, rn, D, m, target, c->opt.max_iters - iters, &go, s)) return e;
+    iters += go.iters;
+    refine++;
+    CK(axpby(X, 1.0, D, 1.0, N, s));
+    if (int e = residual(&rn2)) return e;
+    const double rnew = std::sqrt(rn2);
+    if (!std::isfinite(rnew)) return LMDG_ERR_BREAKDOWN;
+    if (go.breakdown && rnew > c->opt.tol * r0 && rnew >= rn) { rn = rnew; status = LMDG_ERR_BREAKDOWN; break; }
+    rn = rnew;
+  }
+  // outputs: phi from the partial reductions of the last FP64 sweep (at the final x)
+  if (phi) {
+    double *P = (flags & LMDG_HOST_PTRS) ? c->vec[5] : phi;
+    if (c->variant == LMDG_STD) {
+      CK(cudaMemcpyAsync(P, X, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    } else {
+      const int bs = 256, gs = (c->nx + bs - 1) / bs, Pn = 4 * c->g64.groups;
+      const double *part = reinterpret_cast<const double *>(c->part);
+      if (c->variant == LMDG_LM) phi_kernel<double, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
+      else phi_kernel<double, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
+      CK(cudaGetLastError());
+    }
+    if (flags & LMDG_HOST_PTRS) CK(cudaMemcpyAsync(phi, P, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  }
+  if (x) CK(cudaMemcpyAsync(x, X, sizeof(double) * N,
+                            (flags & LMDG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  if (fp32) {
+    // recovery sweep in the working precision: angular unknowns stored as float (or bfloat16)
+    if (int e = sweep_prec(c, 1, X, c->vec[1], 1, true, bf16, s)) return e;
+  }
+  if (int e = check_error_word(c, s)) return e;
+  if (st) {
+    st->iters = iters;
+    st->refinements = fp32 ? refine : 0;
+    st->sweeps_fp64 = c->sweeps64;
+    st->sweeps_fp32 = c->sweeps32;
+    st->resid0 = r0;
+    st->resid = rn;
+    st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    st->sweep_ms = 0;
+  }
+  return status;
+}
+
+int lmdg_b11_apply(lmdg_ctx *c, const double *x, double *y, int flags, void *stream) {
+  if (!c || !x || !y) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const size_t N3 = 3 * (size_t)c->nx;
+  const double A4[4] = {c->Ax[0], c->Ax[1], c->Ay[0], c->Ay[1]};
+  if (flags & LMDG_HOST_PTRS) {
+    if (int e = ensure_krylov(c, c->opt.restart)) return e;
+    CK(cudaMemcpyAsync(c->vec[4], x, sizeof(double) * N3, cudaMemcpyHostToDevice, s));
+    CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, c->vec[4], c->vec[5], s));
+    CK(cudaMemcpyAsync(y, c->vec[5], sizeof(double) * N3, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+  }
+  CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, x, y, s));
+  return 0;
+}
+
+int lmdg_b11_solve(lmdg_ctx *c, const double *r, double *z, double tol, int *iters, int flags, void *stream) {
+  if (!c || !r || !z || !(tol > 0)) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  if (int e = ensure_krylov(c, c->opt.restart)) return e;
+  const size_t N3 = 3 * (size_t)c->nx;
+  const double A4[4] = {c->Ax[0], c->Ax[1], c->Ay[0], c->Ay[1]};
+  double *Z = c->vec[0], *Rr = c->vec[1], *Pp = c->vec[2], *Ap = c->vec[3];
+  double *partial = c->red, *out = c->red + mdot_partial_len(c->red_len);
+  CK(cudaMemcpyAsync(Rr, r, sizeof(double) * N3,
+                     (flags & LMDG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(Z, 0, sizeof(double) * N3, s));
+  CK(cudaMemcpyAsync(Pp, Rr, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s));
+  auto dot = [&](const double *a, const double *b, double *res) -> int {
+    CK(mdot(a, N3, 1, b, N3, partial, out, 0, s));
+    CK(cudaMemcpyAsync(c->red_h, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *res = c->red_h[0];
+    return 0;
+  };
+  double rr = 0;
+  if (int e = dot(Rr, Rr, &rr)) return e;
+  const double stop = tol * tol * rr;
+  int it = 0;
+  const int maxit = 100000;
+  while (rr > stop && it < maxit) {
+    CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, Pp, Ap, s));
+    double pap = 0;
+    if (int e = dot(Pp, Ap, &pap)) return e;
+    if (!(pap > 0)) return LMDG_ERR_BREAKDOWN;
+    const double alpha = rr / pap;
+    CK(axpby(Z, alpha, Pp, 1.0, N3, s));
+    CK(axpby(Rr, -alpha, Ap, 1.0, N3, s));
+    double rr2 = 0;
+    if (int e = dot(Rr, Rr, &rr2)) return e;
+    CK(axpby(Pp, 1.0, Rr, rr2 / rr, N3, s));
+    rr = rr2;
+    ++it;
+  }
+  if (iters) *iters = it;
+  CK(cudaMemcpyAsync(z, Z, sizeof(double) * N3,
+                     (flags & LMDG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return rr > stop ? LMDG_ERR_NOTCONV : 0;
+}
+
+int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double *dq, double *J, lmdg_stats *st,
+                 int flags, void *stream) {
+  (void)g; (void)dss; (void)dsa; (void)dq; (void)J; (void)st; (void)flags; (void)stream;
+  if (!c) return LMDG_ERR_ARG;
+  return LMDG_ERR_STATE;
+}
+
+}  // extern "C"

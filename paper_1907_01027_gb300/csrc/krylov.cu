@@ -1,0 +1,208 @@
+// Vector kernels for GMRES (classical Gram-Schmidt applied twice) and conjugate gradients, plus the B11
+// stencil.  All reductions are two-pass with a fixed block count and a fixed summation order, so results
+// are bitwise reproducible run to run.
+#include "lmdg_internal.h"
+#include "krylov.h"
+
+namespace lmdg {
+
+namespace {
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kChunk = 8;         // vectors reduced per pass over w
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+}  // namespace
+
+// partial[b * nv + i] = sum over this block's slice of V_i[k] * w[k], i < nv
+__global__ void mdot_kernel(const double *__restrict__ V, size_t ldv, int nv, const double *__restrict__ w,
+                            size_t N, double *__restrict__ partial) {
+  __shared__ double sh[kRedThreads / 32][kChunk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < nv; c0 += kChunk) {
+    const int nc = min(kChunk, nv - c0);
+    double acc[kChunk];
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c) acc[c] = 0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+      const double wk = w[k];
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c)
+        if (c < nc) acc[c] = fma(V[(size_t)(c0 + c) * ldv + k], wk, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c) {
+      const double v = warp_sum(acc[c]);
+      if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      double s = 0;
+      for (int ww = 0; ww < kRedThreads / 32; ++ww) s += sh[ww][threadIdx.x];
+      partial[(size_t)blockIdx.x * nv + c0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] = scale * sum_b partial[b * nv + i]   (+ out[i] if accumulate)
+__global__ void mdot_fin_kernel(const double *__restrict__ partial, int nb, int nv, double *__restrict__ out,
+                                int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  double s = 0;
+  for (int b = 0; b < nb; ++b) s += partial[(size_t)b * nv + i];
+  out[i] = accumulate ? out[i] + s : s;
+}
+
+// w -= sum_i V_i coef_i
+__global__ void maxpy_kernel(double *__restrict__ w, const double *__restrict__ V, size_t ldv, int nv,
+                             const double *__restrict__ coef, size_t N) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+    double s = w[k];
+    for (int i = 0; i < nv; ++i) s = fma(-coef[i], V[(size_t)i * ldv + k], s);
+    w[k] = s;
+  }
+}
+
+// y = x * (1 / *nrm)  (nrm on the device)
+__global__ void scale_by_inv_kernel(double *__restrict__ y, const double *__restrict__ x,
+                                    const double *__restrict__ nrm2, size_t N) {
+  const double inv = 1.0 / sqrt(*nrm2);
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+    y[k] = x[k] * inv;
+}
+
+__global__ void axpby_kernel(double *__restrict__ y, double a, const double *__restrict__ x, double b, size_t N) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+    y[k] = fma(a, x[k], b * y[k]);
+}
+
+// y = Minv x for the right preconditioner diag(I, diag(B11))^-1 on [nx][4] vectors (mode 1), copy (mode 0)
+__global__ void precond_kernel(double *__restrict__ y, const double *__restrict__ x,
+                               const double *__restrict__ diag, int nx, int mode) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  double2 va = reinterpret_cast<const double2 *>(x)[2 * K];
+  double2 vb = reinterpret_cast<const double2 *>(x)[2 * K + 1];
+  if (mode == 1) {
+    va.y /= diag[3 * (size_t)K];
+    vb.x /= diag[3 * (size_t)K + 1];
+    vb.y /= diag[3 * (size_t)K + 2];
+  }
+  reinterpret_cast<double2 *>(y)[2 * K] = va;
+  reinterpret_cast<double2 *>(y)[2 * K + 1] = vb;
+}
+
+// B11 = Sigma L11 Sigma^T - Sigma M1 on slope fields u = (c1, c2, c3) per cell (eq-lmdg-psi1):
+//   (B11 u)_r(K) = eps sigma_a int_K u b_r + sum over faces F of K of
+//        [ (outflow weight of F) int_F u^K b_r  -  (inflow weight of F) int_F u^nbr b_r ],
+// where for the east face the outflow weight is Ax+ = sum_{Omega_x>0} w Omega_x and the inflow weight is
+// Ax- = sum_{Omega_x<0} w |Omega_x| (mirror for west, likewise y), and u^nbr = 0 outside the domain.  The
+// volume streaming term vanishes because sum_l w_l Omega_l = 0 (eq-polyquad (ii)).  Face integrals of the
+// slope basis (xi, eta, xi eta), with s = +-1 the side of the face:
+//   x-face (xi = s): traces (s, eta, s eta): int b_r b_q ds = h [[1,0,0],[0,1/3,s/3],[0,s/3,1/3]] with the
+//   neighbour's trace (-s, eta, -s eta) entering as h [[-1,0,0],[0,1/3,-s/3],[0,s/3,-1/3]]  (rows own, cols nbr)
+__global__ void b11_kernel(int n, double h, double eps, const double *__restrict__ sigma_a, double Axp,
+                           double Axm, double Ayp, double Aym, const double *__restrict__ u,
+                           double *__restrict__ y) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= n * n) return;
+  const int i = K % n, j = K / n;
+  const double *uk = u + 3 * (size_t)K;
+  const double c1 = uk[0], c2 = uk[1], c3 = uk[2];
+  const double m = eps * sigma_a[K] * h * h;
+  double y1 = m * c1 / 3.0, y2 = m * c2 / 3.0, y3 = m * c3 / 9.0;
+  // x faces: s = +1 east (outflow weight Axp, inflow Axm), s = -1 west (outflow Axm, inflow Axp)
+  for (int side = 0; side < 2; ++side) {
+    const double s = side == 0 ? 1.0 : -1.0;
+    const double wo = side == 0 ? Axp : Axm, wi = side == 0 ? Axm : Axp;
+    const int in = side == 0 ? i + 1 : i - 1;
+    // own trace: (c1 s) + (c2 + s c3) eta ; test traces b1 = s, b2 = eta, b3 = s eta
+    const double o0 = c1 * s, o1 = c2 + s * c3;
+    y1 += wo * h * (s * o0);
+    y2 += wo * h * (o1 / 3.0);
+    y3 += wo * h * (s * o1 / 3.0);
+    if (in >= 0 && in < n) {
+      const double *un = u + 3 * (size_t)(j * n + in);
+      // neighbour trace on the shared face (its xi = -s): (-s n1) + (n2 - s n3) eta
+      const double e0 = -s * un[0], e1 = un[1] - s * un[2];
+      y1 -= wi * h * (s * e0);
+      y2 -= wi * h * (e1 / 3.0);
+      y3 -= wi * h * (s * e1 / 3.0);
+    }
+  }
+  for (int side = 0; side < 2; ++side) {
+    const double s = side == 0 ? 1.0 : -1.0;
+    const double wo = side == 0 ? Ayp : Aym, wi = side == 0 ? Aym : Ayp;
+    const int jn = side == 0 ? j + 1 : j - 1;
+    // own trace at eta = s: (c2 s) + (c1 + s c3) xi ; tests b1 = xi, b2 = s, b3 = s xi
+    const double o0 = c2 * s, o1 = c1 + s * c3;
+    y1 += wo * h * (o1 / 3.0);
+    y2 += wo * h * (s * o0);
+    y3 += wo * h * (s * o1 / 3.0);
+    if (jn >= 0 && jn < n) {
+      const double *un = u + 3 * (size_t)(jn * n + i);
+      const double e0 = -s * un[1], e1 = un[0] - s * un[2];
+      y1 -= wi * h * (e1 / 3.0);
+      y2 -= wi * h * (s * e0);
+      y3 -= wi * h * (s * e1 / 3.0);
+    }
+  }
+  double *yk = y + 3 * (size_t)K;
+  yk[0] = y1; yk[1] = y2; yk[2] = y3;
+}
+
+__global__ void to_double_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, size_t N) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+    if (kind == 1) y[k] = (double)reinterpret_cast<const float *>(x)[k];
+    else if (kind == 2) y[k] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
+    else y[k] = reinterpret_cast<const double *>(x)[k];
+  }
+}
+
+// ------------------------------------------------------------------------------------------ host wrappers
+static int grid_for(size_t N) {
+  size_t g = (N + 255) / 256;
+  return (int)(g < 2048 ? (g == 0 ? 1 : g) : 2048);
+}
+
+cudaError_t mdot(const double *V, size_t ldv, int nv, const double *w, size_t N, double *partial, double *out,
+                 int accumulate, cudaStream_t s) {
+  mdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, nv, w, N, partial);
+  mdot_fin_kernel<<<(nv + 127) / 128, 128, 0, s>>>(partial, kRedBlocks, nv, out, accumulate);
+  return cudaGetLastError();
+}
+size_t mdot_partial_len(int nvmax) { return (size_t)kRedBlocks * nvmax; }
+
+cudaError_t maxpy(double *w, const double *V, size_t ldv, int nv, const double *coef, size_t N, cudaStream_t s) {
+  maxpy_kernel<<<grid_for(N), 256, 0, s>>>(w, V, ldv, nv, coef, N);
+  return cudaGetLastError();
+}
+cudaError_t scale_by_inv(double *y, const double *x, const double *nrm2, size_t N, cudaStream_t s) {
+  scale_by_inv_kernel<<<grid_for(N), 256, 0, s>>>(y, x, nrm2, N);
+  return cudaGetLastError();
+}
+cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cudaStream_t s) {
+  axpby_kernel<<<grid_for(N), 256, 0, s>>>(y, a, x, b, N);
+  return cudaGetLastError();
+}
+cudaError_t precond(double *y, const double *x, const double *diag, int nx, int mode, cudaStream_t s) {
+  precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, diag, nx, mode);
+  return cudaGetLastError();
+}
+cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
+                      double *y, cudaStream_t s) {
+  b11_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
+  return cudaGetLastError();
+}
+cudaError_t to_double(double *y, const void *x, int kind, size_t N, cudaStream_t s) {
+  to_double_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, N);
+  return cudaGetLastError();
+}
+
+}  // namespace lmdg

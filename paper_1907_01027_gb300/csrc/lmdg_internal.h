@@ -1,0 +1,97 @@
+// Internal declarations of liblmdg (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include "../../include/lmdg.h"
+
+namespace lmdg {
+
+// Per-precision copies of the problem data, directions sorted by quadrant (+,+), (-,+), (-,-), (+,-).
+template <typename T>
+struct ProblemData {
+  T *ox = nullptr, *oy = nullptr, *w = nullptr;  // [nang] sorted
+  T *sigt = nullptr;                              // [nx] sigma_s/eps + eps sigma_a
+  T *sse = nullptr;                               // [nx] sigma_s/eps
+  T *q = nullptr;                                 // [nx][4] or [nang(sorted)][nx][4]
+  T *alpha = nullptr;                             // [nang(sorted)][4][n][2] or null
+};
+
+// Sweep launch geometry: one CTA per (quadrant, angle group, strip of 32 rows); warps of a CTA hold
+// disjoint angles of the group, each warp up to kMaxA angles processed per step.
+struct SweepGeom {
+  int groups;      // angle groups per quadrant
+  int warps;       // warps per CTA
+  int apw;         // angles per warp (<= kMaxA)
+  int strips;      // ceil(n / 32)
+  int units() const { return 4 * groups * strips; }
+};
+
+constexpr int kMaxA = 4;        // compile-time cap on angles per warp
+constexpr int kPublish = 8;     // steps between progress publications of a strip
+
+// Arguments of one sweep launch (everything a kernel reads or writes).
+template <typename T>
+struct SweepArgs {
+  int n, nq, nang, nx;
+  T h, eps;
+  SweepGeom g;
+  ProblemData<T> pd;
+  int q_per_angle;
+  const double *X;     // [nx][4] input vector (always double)
+  const T *p1ra;       // [nx][2] P1 r_alpha (RLMDG, source sweeps) or null
+  int source;          // 1: add eps q and the inflow data alpha
+  T *part;             // [4*groups][nx][NR] partial reductions, written once each
+  void *psi;           // storing sweep output or null (sorted->user order through perm)
+  int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
+  const int *perm;     // [nang] sorted index -> user index
+  T *ytr;              // [nang][strips][n][3] traces crossing strip boundaries
+  unsigned *ctrl;      // [0] ticket, [1] error, [2 + unit] progress
+  long long spin_limit;
+};
+
+// Host-side launchers (sweep.cu)
+template <typename T>
+cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s);
+
+// y = K x - source * b  from the partial reductions (sweep.cu)
+template <typename T>
+cudaError_t launch_epilogue(int variant, int n, int nx, int P, double h, const T *part, const double *X,
+                            const double *sse, const double *p1ra, const double *sq1, int source,
+                            double *y, cudaStream_t s);
+
+}  // namespace lmdg
+
+// Context
+struct lmdg_ctx {
+  int n = 0, nx = 0, nang = 0, nq = 0, variant = 0, q_layout = 0, has_alpha = 0, dev = 0;
+  double h = 0, eps = 0, x0 = 0, y0 = 0;
+  lmdg_options opt{};
+  int *perm = nullptr;                     // device [nang]
+  int *perm_h = nullptr;                   // host copy
+  lmdg::ProblemData<double> d64;
+  lmdg::ProblemData<float> d32;
+  double *p1ra64 = nullptr;                // [nx][2]
+  float *p1ra32 = nullptr;
+  double *sq1 = nullptr;                   // [nx][3] Sigma Q1
+  double *b11diag = nullptr;               // [nx][3] diagonal of B11 (Jacobi preconditioner)
+  double *sigma_a = nullptr;               // [nx] (B11 stencil)
+  double Ax[2] = {0, 0}, Ay[2] = {0, 0};   // sum of w |Omega_x| over Omega_x > 0 / < 0, likewise y
+  lmdg::SweepGeom g64{}, g32{};
+  void *part = nullptr;                    // partial reductions (double-sized)
+  void *ytr = nullptr;                     // inter-strip traces (double-sized)
+  unsigned *ctrl = nullptr;
+  size_t ctrl_words = 0;
+  void *psi = nullptr;                     // stored angular unknowns
+  int psi_kind = -1;                       // -1 none, 0 double, 1 float, 2 bf16
+  size_t psi_elems = 0;
+  // Krylov workspace
+  double *V = nullptr;                     // (m+1) x N basis
+  double *vec[6] = {nullptr};              // scratch vectors of length N
+  double *red = nullptr;                   // reduction scratch
+  double *red_h = nullptr;                 // pinned host mirror
+  int red_len = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double sweep_ms_acc = 0;
+  int sweeps64 = 0, sweeps32 = 0;
+};
