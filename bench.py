@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the low-memory S_N-DG hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path over the 1024 x 1024, S16 workload with 16 x 16-cell patches of
+sigma_s, sigma_a ~ U[0.1, 10] (seed 1907), q = 1, eps = 1, vacuum inflow: for each scheme (standard Q1-DG,
+LMDG, RLMDG) one lmdg_solve to a 1e-8 relative residual with FP32 sweeps inside FP64 iterative refinement
+(FP64 Arnoldi and residuals), including the recovery sweep that stores the angular unknowns.  The metric is
+transport-sweep cell-angle updates per second over the step (every sweep the solves run, FP32 and FP64);
+time to 1e-8 for the mixed and the FP64 solver is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sweep cell·angle updates/s; GMRES time to 1e-8 resid, mixed vs FP64 (1 GB300)"
+UNIT = "cell-angle updates/s"
+VARIANTS = ("std", "lm", "rlm")
+
+# FP32 operations per cell-angle update in the sweep kernel (counted from the kernel source, FMA = 2;
+# reciprocals count 1): standard Q1 block solve, low-memory row-0 solve + L-row reductions, reconstructed.
+FLOPS_PER_UPDATE = {"std": 104, "lm": 56, "rlm": 70}
+
+
+def workload_config():
+    return {"workload": "1024x1024 cells, S16 level-symmetric (144 directions), sigma_s and sigma_a piecewise "
+                        "constant on 16x16-cell patches ~ U[0.1,10] (seed 1907), q=1, eps=1, vacuum inflow; "
+                        "per step one mixed-precision GMRES(30) solve to 1e-8 for each of Q1-DG, LMDG, RLMDG",
+            "n": 1024, "directions": 144, "eps": 1.0, "restart": 30, "tol": 1e-8,
+            "l2": "flushed between steps by a 512 MB write"}
+
+
+def dist_setup(ngpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        return rank, ws, dist
+    return 0, 1, None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{idx}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}", "--format=csv",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        try:
+            lines = [l.strip() for l in open(self.path) if l.strip() and not l.startswith("index")]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax = float(f[2].split()[0])
+            except Exception:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_oracle_sample(p, per_variant=16, threads=None):
+    """Oracle transport sweeps (its per-direction upwind solves) on a subset of the workload's directions:
+    returns (cell-angle updates/s, cores, description)."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle.sweeps import SweepOracle
+    so = SweepOracle(p, threads=threads)
+    cores = so.threads
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((p.nx, 4))
+    step = max(1, p.nang // per_variant)
+    angles = list(range(0, p.nang, step))[:per_variant]
+    jobs = []
+    for l in angles:
+        jobs.append(lambda l=l: so.Linv(l, so.M(l, X) + so.Q(l)))
+        jobs.append(lambda l=l: so.L00inv(l, so.M0(l, X[:, 0]) + so.L01SigT(l, X[:, 1:])))
+        jobs.append(lambda l=l: so.Lt00inv(l, so.M0(l, X[:, 0]) + so.L01SigT(l, X[:, 1:])))
+    t = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda f: f(), jobs))
+    dt = time.perf_counter() - t
+    ups = len(jobs) * p.nx
+    desc = (f"oracle upwind sweeps (Q1 block, L00, Ltilde00 with reconstruction) for {len(angles)} of "
+            f"{p.nang} directions each on the {p.n}x{p.n} mesh, {len(jobs)} sweeps on {cores} threads")
+    return ups / dt, cores, desc, dt
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    from workloads.problems import config4
+    p = config4(eps=1.0)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(p, per_variant=2)
+    vals, times = [], []
+    desc = cores = None
+    for _ in range(args.steps):
+        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=4)
+        vals.append(v)
+        times.append(dt)
+    value = len(vals) / sum(1.0 / v for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, ws, dist):
+    import numpy as np
+    import torch
+    from paper_1907_01027_gb300 import Context, FP32, FP64, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
+    from paper_1907_01027_gb300 import buildlib
+    from workloads.problems import config4
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    buildlib.build()
+    p = config4(eps=1.0)
+    upd = p.nx * p.nang
+    ctxs = {v: Context(p, v, precision=FP32, tol=1e-8, device=local) for v in VARIANTS}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(stats_acc=None):
+        for v in VARIANTS:
+            _, _, st, rc = ctxs[v].solve(want_x=False, want_phi=True, device=True)
+            if rc != 0:
+                raise RuntimeError(f"{v} solve did not converge: {st}")
+            if stats_acc is not None:
+                stats_acc.append((v, st))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stats = []
+    durations = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0.record()
+            step(stats)
+            e1.record()
+            torch.cuda.synchronize()
+            durations.append(e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = sum(durations)
+    sweeps = sum(st["sweeps_fp32"] + st["sweeps_fp64"] for _, st in stats)
+    updates = sweeps * upd
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        updates = float(u.item())
+    value = updates / (total_ms / 1e3)
+    launches = sum(st["launches"] for _, st in stats)
+
+    # roofline of the dominant kernel (the FP32 sweep inside the solves), live from the timed region
+    f32_ms = sum(st["sweep_ms_fp32"] for _, st in stats)
+    f32_n = sum(st["sweeps_fp32"] for _, st in stats)
+    f64_ms = sum(st["sweep_ms_fp64"] for _, st in stats)
+    f64_n = sum(st["sweeps_fp64"] for _, st in stats)
+    flops = sum(FLOPS_PER_UPDATE[v] * st["sweeps_fp32"] * upd for v, st in stats)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = flops / (f32_ms / 1e3) / 1e12 if f32_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "sweep_kernel<float> (all three schemes, non-storing)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "peak_source": "FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n,
+                "flops_per_update": FLOPS_PER_UPDATE,
+                "fp64_sweep_avg_ms": f64_ms / max(1, f64_n), "fp64_sweeps": f64_n}
+    clocks = clk.summary()
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps / f64 refinement", "data": "synthetic",
+           "config": workload_config(), "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
+
+    # time to 1e-8: mixed (from the timed region) vs FP64 (one solve each, after it)
+    ttr = {}
+    for v in VARIANTS:
+        mixed = [st for vv, st in stats if vv == v]
+        ttr[v] = {"mixed_ms": sum(s["time_ms"] for s in mixed) / len(mixed),
+                  "mixed_iters": mixed[-1]["iters"], "mixed_refinements": mixed[-1]["refinements"],
+                  "mixed_sweeps_fp32": mixed[-1]["sweeps_fp32"], "mixed_sweeps_fp64": mixed[-1]["sweeps_fp64"]}
+    if not args.skip_fp64:
+        for v in VARIANTS:
+            ctx = Context(p, v, precision=FP64, tol=1e-8, device=local)
+            torch.cuda.synchronize()
+            e0.record()
+            _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ttr[v].update({"fp64_ms": e0.elapsed_time(e1), "fp64_iters": st["iters"], "fp64_status": rc,
+                           "fp64_sweep_avg_ms": st["sweep_ms_fp64"] / max(1, st["sweeps_fp64"])})
+            ctx.close()
+    out["gmres_time_to_1e-8"] = ttr
+
+    # storing sweep (recovery): HBM roofline of the FP32 Q1-DG sweep that writes psi (16 B per update)
+    x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    c = ctxs["std"]
+    for _ in range(3):
+        c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+    torch.cuda.synchronize()
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        flush.fill_(1.0)
+        c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+    e1.record()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(reps):
+        flush.fill_(1.0)
+    e3.record()
+    torch.cuda.synchronize()
+    ms_store = (e0.elapsed_time(e1) - e2.elapsed_time(e3)) / reps
+    bytes_store = upd * 16 + p.nx * (32 + 4 * 3 + 16) + p.nx * 32
+    hbm = peaks().get("hbm_gbs")
+    ach = bytes_store / (ms_store / 1e3) / 1e9
+    out["roofline_storing_sweep"] = {"bound": "hbm", "kernel": "sweep_kernel<float, Q1-DG, store> + epilogue",
+                                     "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                     "frac": ach / hbm if hbm else None, "ms": ms_store,
+                                     "algorithmic_bytes": bytes_store,
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    # end to end through the public API with host buffers: setup from host arrays, solve, phi back to host
+    e2e_ms, e2e_upd = 0.0, 0
+    h2d = d2h = 0
+    for k in range(max(1, args.steps)):
+        for v in VARIANTS:
+            t0 = time.perf_counter()
+            ctx = Context(p, v, precision=FP32, tol=1e-8, device=local)
+            _, phi, st, rc = ctx.solve(want_x=False, want_phi=True, device=False)
+            ctx.close()
+            torch.cuda.synchronize()
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+            e2e_upd += (st["sweeps_fp32"] + st["sweeps_fp64"]) * upd
+            if k == 0:
+                h2d += 8 * (3 * p.nang + 2 * p.nx + 4 * p.nx)
+                d2h += phi.nbytes
+    out["e2e"] = {"value": e2e_upd / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h,
+                  "what": "lmdg_setup from host arrays + lmdg_solve (LMDG_HOST_PTRS, phi to host) + destroy, "
+                          "three schemes per step"}
+
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=16)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                               "seconds": dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for c in ctxs.values():
+        c.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, ws, dist = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, ws)
+        return run_gpu(args, rank, ws, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -97,7 +97,9 @@ typedef struct {
   double resid0;       /* ||r_0|| */
   double resid;        /* final ||b - K x|| from an FP64 sweep */
   double time_ms;      /* wall time of the call (host clock) */
-  double sweep_ms;     /* device time spent in sweep kernels (CUDA events) */
+  double sweep_ms_fp64;/* device time inside FP64 sweep kernels (CUDA events around each launch) */
+  double sweep_ms_fp32;/* device time inside FP32 sweep kernels */
+  long long launches;  /* kernels launched by the call */
 } lmdg_stats;
 
 /* Fill *opt with the defaults listed above. */

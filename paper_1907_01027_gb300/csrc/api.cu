@@ -71,6 +71,16 @@ SweepGeom choose_geom(int n, int nq, int nsm, bool fp64) {
 
 size_t part_elems(const SweepGeom &g, int nx) { return (size_t)4 * g.groups * nx * 6; }
 
+// Add the device time of the last recorded sweep launch to its precision's total (after a synchronisation,
+// or waiting for it when wait is set).
+void harvest(lmdg_ctx *c, bool wait) {
+  if (c->ev_pending < 0) return;
+  if (wait) cudaEventSynchronize(c->ev1);
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->sweep_ms[c->ev_pending] += ms;
+  c->ev_pending = -1;
+}
+
 template <typename T>
 int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s) {
   SweepArgs<T> a{};
@@ -105,10 +115,15 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     a.psi = c->psi;
     a.psi_bf16 = kind == 2;
   }
-  const bool timed = c->ev0 != nullptr;
-  if (timed) CK(cudaEventRecord(c->ev0, s));
+  if (!c->ev0) {
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+  }
+  if (c->ev_pending >= 0) harvest(c, true);
+  CK(cudaEventRecord(c->ev0, s));
   CK(launch_sweep<T>(c->variant, a, s));
-  if (timed) CK(cudaEventRecord(c->ev1, s));
+  CK(cudaEventRecord(c->ev1, s));
+  c->ev_pending = f64 ? 0 : 1;
   CK(launch_epilogue<T>(c->variant, c->n, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->p1ra64,
                         c->sq1, source, y, s));
   if (f64) c->sweeps64++; else c->sweeps32++;
@@ -124,6 +139,7 @@ int check_error_word(lmdg_ctx *c, cudaStream_t s) {
   unsigned err = 0;
   CK(cudaMemcpyAsync(&err, c->ctrl + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  harvest(c, false);
   return err ? LMDG_ERR_TIMEOUT : 0;
 }
 
@@ -517,8 +533,9 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
   const int bf16 = c->opt.precision == LMDG_FP32_BF16STORE;
   double *X = c->vec[2], *R = c->vec[3], *D = c->vec[4];
   c->sweeps64 = c->sweeps32 = 0;
-  if (!c->ev0) { CK(cudaEventCreate(&c->ev0)); CK(cudaEventCreate(&c->ev1)); }
-  c->sweep_ms_acc = 0;
+  harvest(c, true);
+  c->sweep_ms[0] = c->sweep_ms[1] = 0;
+  const long long launches0 = launch_count();
   if (x0) CK(cudaMemcpyAsync(X, x0, sizeof(double) * N,
                              (flags & LMDG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(X, 0, sizeof(double) * N, s));
@@ -557,6 +574,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     } else {
       const int bs = 256, gs = (c->nx + bs - 1) / bs, Pn = 4 * c->g64.groups;
       const double *part = reinterpret_cast<const double *>(c->part);
+      add_launches(1);
       if (c->variant == LMDG_LM) phi_kernel<double, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
       else phi_kernel<double, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
       CK(cudaGetLastError());
@@ -578,7 +596,10 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     st->resid0 = r0;
     st->resid = rn;
     st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    st->sweep_ms = 0;
+    harvest(c, true);
+    st->sweep_ms_fp64 = c->sweep_ms[0];
+    st->sweep_ms_fp32 = c->sweep_ms[1];
+    st->launches = launch_count() - launches0;
   }
   return status;
 }

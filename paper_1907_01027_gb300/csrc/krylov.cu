@@ -3,6 +3,7 @@
 // are bitwise reproducible run to run.
 #include "lmdg_internal.h"
 #include "krylov.h"
+#include <atomic>
 
 namespace lmdg {
 
@@ -166,6 +167,10 @@ __global__ void to_double_kernel(double *__restrict__ y, const void *__restrict_
 }
 
 // ------------------------------------------------------------------------------------------ host wrappers
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void add_launches(long long k) { g_launches += k; }
+
 static int grid_for(size_t N) {
   size_t g = (N + 255) / 256;
   return (int)(g < 2048 ? (g == 0 ? 1 : g) : 2048);
@@ -173,6 +178,7 @@ static int grid_for(size_t N) {
 
 cudaError_t mdot(const double *V, size_t ldv, int nv, const double *w, size_t N, double *partial, double *out,
                  int accumulate, cudaStream_t s) {
+  add_launches(2);
   mdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, nv, w, N, partial);
   mdot_fin_kernel<<<(nv + 127) / 128, 128, 0, s>>>(partial, kRedBlocks, nv, out, accumulate);
   return cudaGetLastError();
@@ -180,27 +186,33 @@ cudaError_t mdot(const double *V, size_t ldv, int nv, const double *w, size_t N,
 size_t mdot_partial_len(int nvmax) { return (size_t)kRedBlocks * nvmax; }
 
 cudaError_t maxpy(double *w, const double *V, size_t ldv, int nv, const double *coef, size_t N, cudaStream_t s) {
+  add_launches(1);
   maxpy_kernel<<<grid_for(N), 256, 0, s>>>(w, V, ldv, nv, coef, N);
   return cudaGetLastError();
 }
 cudaError_t scale_by_inv(double *y, const double *x, const double *nrm2, size_t N, cudaStream_t s) {
+  add_launches(1);
   scale_by_inv_kernel<<<grid_for(N), 256, 0, s>>>(y, x, nrm2, N);
   return cudaGetLastError();
 }
 cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cudaStream_t s) {
+  add_launches(1);
   axpby_kernel<<<grid_for(N), 256, 0, s>>>(y, a, x, b, N);
   return cudaGetLastError();
 }
 cudaError_t precond(double *y, const double *x, const double *diag, int nx, int mode, cudaStream_t s) {
+  add_launches(1);
   precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, diag, nx, mode);
   return cudaGetLastError();
 }
 cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
                       double *y, cudaStream_t s) {
+  add_launches(1);
   b11_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
   return cudaGetLastError();
 }
 cudaError_t to_double(double *y, const void *x, int kind, size_t N, cudaStream_t s) {
+  add_launches(1);
   to_double_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, N);
   return cudaGetLastError();
 }

@@ -50,6 +50,10 @@ struct SweepArgs {
   long long spin_limit;
 };
 
+// Number of kernels launched by this library (all host wrappers add to it).
+long long launch_count();
+void add_launches(long long k);
+
 // Host-side launchers (sweep.cu)
 template <typename T>
 cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s);
@@ -92,6 +96,8 @@ struct lmdg_ctx {
   double *red_h = nullptr;                 // pinned host mirror
   int red_len = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double sweep_ms_acc = 0;
+  int ev_pending = -1;                     // precision of a recorded, not yet harvested sweep (-1 none)
+  double sweep_ms[2] = {0, 0};             // device time in FP64 / FP32 sweep kernels
+  long long launches = 0;
   int sweeps64 = 0, sweeps32 = 0;
 };

@@ -402,6 +402,7 @@ static cudaError_t launch_var(const SweepArgs<T> &a, bool store, cudaStream_t s)
   const dim3 grid(a.g.units()), block(a.g.warps * 32);
   cudaError_t e = cudaMemsetAsync(a.ctrl, 0, (2 + (size_t)a.g.units()) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
+  add_launches(1);
   if (store) sweep_kernel<T, VAR, true><<<grid, block, smem, s>>>(a);
   else sweep_kernel<T, VAR, false><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
@@ -423,6 +424,7 @@ cudaError_t launch_epilogue(int variant, int n, int nx, int P, double h, const T
                             cudaStream_t s) {
   (void)n;
   const int bs = 256, gs = (nx + bs - 1) / bs;
+  add_launches(1);
   switch (variant) {
     case LMDG_STD: epilogue_kernel<T, 0><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, p1ra, sq1, source, y); break;
     case LMDG_LM: epilogue_kernel<T, 1><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, p1ra, sq1, source, y); break;

@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
                 ("sweeps_fp32", ctypes.c_int), ("resid0", ctypes.c_double), ("resid", ctypes.c_double),
-                ("time_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double)]
+                ("time_ms", ctypes.c_double), ("sweep_ms_fp64", ctypes.c_double),
+                ("sweep_ms_fp32", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
