@@ -321,6 +321,30 @@ def run_gpu(args, rank, ws, dist):
     return 0
 
 
+def run_profile(args):
+    """Small case for ncu: 512x512 cells, S16, the bench media; one FP32 LMDG sweep (non-storing) and one FP32
+    Q1-DG storing sweep (psi 604 MB, larger than L2), after one untimed sweep of each."""
+    import torch
+    from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
+    from workloads.problems import config4
+    torch.cuda.set_device(0)
+    p = config4(eps=1.0, n=512)
+    lm = Context(p, "lm", precision=FP32)
+    st = Context(p, "std", precision=FP32)
+    x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    lm.sweep(x, y, flags=SWEEP_FP32)
+    st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+    torch.cuda.synchronize()
+    lm.sweep(x, y, flags=SWEEP_FP32)
+    st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+    torch.cuda.synchronize()
+    lm.close()
+    st.close()
+    print("profile case done", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,7 +353,10 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small fixed case for ncu captures")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         args.warmup = 3
     rank, ws, dist = dist_setup(args.gpus)
