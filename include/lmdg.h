@@ -168,6 +168,28 @@ int lmdg_b11_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, void *s
 int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *iters, int flags,
                    void *stream);
 
+/* Operator application that allocates nothing (no counterpart in the paper: it is a deployment variant of
+ * lmdg_sweep's homogeneous mode, y = K x, for callers that cannot call cudaMalloc -- e.g. a host framework
+ * that owns all device memory through its own pool, a latency-critical loop that cannot take cudaMalloc's
+ * implicit device synchronisation, or an embedding runtime that hands over only input and output buffers).
+ *   variant          : LMDG_STD, LMDG_LM or LMDG_RLM.
+ *   n, h             : n x n cells of side h.
+ *   n_omega, ox, oy, w : DEVICE arrays [n_omega] of directions and weights, grouped by quadrant in the order
+ *                      (+,+), (-,+), (-,-), (+,-) with n_omega/4 directions each (not checked: the arrays
+ *                      stay on the device); n_omega a multiple of 4, at most 1024.
+ *   sigma_t          : DEVICE [n*n] sigma_s/eps + eps sigma_a;  sigma_s_over_eps : DEVICE [n*n] sigma_s/eps.
+ *   x, y             : DEVICE [n*n][4] doubles, 16-byte aligned (x: input, y: output, distinct).
+ *   spin_limit       : polls of a readiness flag before giving up with LMDG_ERR_TIMEOUT.
+ * The sweep's scratch (strip traces, partial reductions, control words) is a fixed 16 MiB device array
+ * reserved on every GPU that loads the library until the process exits; problems whose scratch does not fit
+ * (roughly n*n*(96 or 192) + n_omega*n^2*0.75 bytes) are rejected with LMDG_ERR_ARG.  The first call on a
+ * device (with that device current) looks the array up and initialises it: make that call before any stream
+ * capture.  Calls share the array; calls whose kernels overlap on the GPU race and must be serialised.  The
+ * call synchronises the stream to read the sweep's error word. */
+int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, const double *ox, const double *oy,
+                       const double *w, const double *sigma_t, const double *sigma_s_over_eps,
+                       const double *x, double *y, long long spin_limit, void *stream);
+
 /* Problem sizes of a context: n, n_Omega, variant. */
 int lmdg_info(const lmdg_ctx *ctx, int *n, int *n_omega, int *variant);
 
