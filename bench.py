@@ -322,8 +322,8 @@ def run_gpu(args, rank, ws, dist):
 
 
 def run_profile(args):
-    """Small case for ncu: 512x512 cells, S16, the bench media; one FP32 LMDG sweep (non-storing) and one FP32
-    Q1-DG storing sweep (psi 604 MB, larger than L2), after one untimed sweep of each."""
+    """Small case for ncu: 512x512 cells, S16, the bench media; one FP32 LMDG sweep (non-storing), one FP32
+    Q1-DG storing sweep (psi 604 MB, larger than L2) and one FP64 LMDG sweep, after one untimed sweep of each."""
     import torch
     from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
     from workloads.problems import config4
@@ -333,12 +333,11 @@ def run_profile(args):
     st = Context(p, "std", precision=FP32)
     x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
-    lm.sweep(x, y, flags=SWEEP_FP32)
-    st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
-    torch.cuda.synchronize()
-    lm.sweep(x, y, flags=SWEEP_FP32)
-    st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
-    torch.cuda.synchronize()
+    for _ in range(2):
+        lm.sweep(x, y, flags=SWEEP_FP32)
+        st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+        lm.sweep(x, y, flags=0)
+        torch.cuda.synchronize()
     lm.close()
     st.close()
     print("profile case done", flush=True)

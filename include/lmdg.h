@@ -182,7 +182,7 @@ int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *i
  *   spin_limit       : polls of a readiness flag before giving up with LMDG_ERR_TIMEOUT.
  * The sweep's scratch (strip traces, partial reductions, control words) is a fixed 16 MiB device array
  * reserved on every GPU that loads the library until the process exits; problems whose scratch does not fit
- * (roughly n*n*(96 or 192) + n_omega*n^2*0.75 bytes) are rejected with LMDG_ERR_ARG.  The first call on a
+ * (roughly n*n*(136 to 232) + n_omega*n^2*0.75 bytes) are rejected with LMDG_ERR_ARG.  The first call on a
  * device (with that device current) looks the array up and initialises it: make that call before any stream
  * capture.  Calls share the array; calls whose kernels overlap on the GPU race and must be serialised.  The
  * call synchronises the stream to read the sweep's error word. */

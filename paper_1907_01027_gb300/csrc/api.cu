@@ -39,36 +39,6 @@ void free_pd(ProblemData<T> &p) {
   p = ProblemData<T>();
 }
 
-// Launch geometry: enough (quadrant, group, strip) CTAs to cover ~2 per SM, at most 8 warps per CTA and
-// kMaxA directions per warp.  LMDG_SWEEP_GEOM="groups,warps,apw" overrides it (tuning only).
-SweepGeom choose_geom(int n, int nq, int nsm, bool fp64) {
-  SweepGeom g;
-  g.strips = (n + 31) / 32;
-  int target = 2 * nsm;
-  int G = std::max(1, std::min(nq, (target + 4 * g.strips - 1) / (4 * g.strips)));
-  int gsize = (nq + G - 1) / G;
-  int apw = std::max(1, std::min(kMaxA, (gsize + 7) / 8));
-  if (fp64 && gsize >= 4 && apw < 2) apw = 2;
-  int W = (gsize + apw - 1) / apw;
-  g.groups = G; g.warps = W; g.apw = apw;
-  if (const char *e = std::getenv("LMDG_SWEEP_GEOM")) {
-    int a = 0, b = 0, c = 0;
-    if (std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a >= 1 && a <= nq && c >= 1 && c <= kMaxA && b >= 1 &&
-        b <= 8) {
-      int gs = (nq + a - 1) / a;
-      if (b * c >= gs && b <= gs) { g.groups = a; g.warps = b; g.apw = c; }
-    }
-  }
-  // every group must be non-empty and every warp must own at least one direction
-  while (g.groups > 1 && (g.groups - 1) * ((nq + g.groups - 1) / g.groups) >= nq) --g.groups;
-  gsize = (nq + g.groups - 1) / g.groups;
-  int last = nq - (g.groups - 1) * gsize;
-  if (g.warps > last) g.warps = last;
-  g.apw = (gsize + g.warps - 1) / g.warps;
-  if (g.apw > kMaxA) { g.apw = kMaxA; g.warps = (gsize + kMaxA - 1) / kMaxA; }
-  return g;
-}
-
 size_t part_elems(const SweepGeom &g, int nx) { return (size_t)4 * g.groups * nx * 6; }
 
 // Add the device time of the last recorded sweep launch to its precision's total (after a synchronisation,
@@ -98,6 +68,8 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.ytr = reinterpret_cast<T *>(c->ytr);
   a.ctrl = c->ctrl;
   a.spin_limit = c->opt.spin_limit;
+  a.cellsrc = reinterpret_cast<const T *>(c->cellsrc);
+  a.cellsh = reinterpret_cast<const T *>(c->cellsh);
   a.psi = nullptr;
   a.psi_bf16 = 0;
   if (store) {
@@ -120,6 +92,15 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     CK(cudaEventCreate(&c->ev1));
   }
   if (c->ev_pending >= 0) harvest(c, true);
+  // the strip traces must hold the empty pattern: initially, after a change of precision (float words sit at
+  // other offsets) and after a sweep that stopped early
+  const int want = f64 ? 0 : 1;
+  if (c->ytr_dirty || c->ytr_prec != want) {
+    if (fill_u32(reinterpret_cast<unsigned *>(c->ytr), kTraceEmpty, c->ytr_words, s) != cudaSuccess)
+      return LMDG_ERR_CUDA;
+    c->ytr_dirty = false;
+    c->ytr_prec = want;
+  }
   CK(cudaEventRecord(c->ev0, s));
   CK(launch_sweep<T>(c->variant, a, s));
   CK(cudaEventRecord(c->ev1, s));
@@ -140,6 +121,7 @@ int check_error_word(lmdg_ctx *c, cudaStream_t s) {
   CK(cudaMemcpyAsync(&err, c->ctrl + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   harvest(c, false);
+  if (err) c->ytr_dirty = true;
   return err ? LMDG_ERR_TIMEOUT : 0;
 }
 
@@ -320,6 +302,7 @@ void lmdg_destroy(lmdg_ctx *c) {
   free_pd(c->d32);
   cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11diag);
   cudaFree(c->sigma_a); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
+  cudaFree(c->cellsrc); cudaFree(c->cellsh);
   cudaFree(c->V);
   for (auto &v : c->vec) cudaFree(v);
   cudaFree(c->red);
@@ -468,14 +451,21 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
   }
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, o.device);
-  c->g64 = choose_geom(n, c->nq, nsm, true);
-  c->g32 = choose_geom(n, c->nq, nsm, false);
+  c->g64 = choose_geom(variant, n, c->nq, true);
+  c->g32 = choose_geom(variant, n, c->nq, false);
+  if (c->g64.units() == 0 || c->g32.units() == 0) return fail(LMDG_ERR_CUDA);
+  if (std::getenv("LMDG_VERBOSE"))
+    std::fprintf(stderr, "lmdg: n=%d n_omega=%d variant=%d fp64 shape groups=%d warps=%d apw=%d | fp32 groups=%d "
+                 "warps=%d apw=%d\n", n, na, variant, c->g64.groups, c->g64.warps, c->g64.apw, c->g32.groups,
+                 c->g32.warps, c->g32.apw);
   const size_t pe = std::max(part_elems(c->g64, c->nx), part_elems(c->g32, c->nx));
   if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   const int strips = (n + 31) / 32;
   if (cudaMalloc(&c->ytr, sizeof(double) * (size_t)na * strips * n * 3) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  c->ytr_words = 2 * (size_t)na * strips * n * 3;
+  c->ytr_dirty = true;
+  if (cudaMalloc(&c->cellsrc, sizeof(double) * 4 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (cudaMalloc(&c->cellsh, sizeof(double) * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   c->ctrl_words = 2 + (size_t)std::max(c->g64.units(), c->g32.units());
   if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);

@@ -10,7 +10,7 @@ namespace lmdg {
 namespace {
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 constexpr int kRedThreads = 256;
-constexpr int kChunk = 8;         // vectors reduced per pass over w
+constexpr int kDotChunk = 8;         // vectors reduced per pass over w
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -22,21 +22,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial[b * nv + i] = sum over this block's slice of V_i[k] * w[k], i < nv
 __global__ void mdot_kernel(const double *__restrict__ V, size_t ldv, int nv, const double *__restrict__ w,
                             size_t N, double *__restrict__ partial) {
-  __shared__ double sh[kRedThreads / 32][kChunk];
+  __shared__ double sh[kRedThreads / 32][kDotChunk];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < nv; c0 += kChunk) {
-    const int nc = min(kChunk, nv - c0);
-    double acc[kChunk];
+  for (int c0 = 0; c0 < nv; c0 += kDotChunk) {
+    const int nc = min(kDotChunk, nv - c0);
+    double acc[kDotChunk];
 #pragma unroll
-    for (int c = 0; c < kChunk; ++c) acc[c] = 0;
+    for (int c = 0; c < kDotChunk; ++c) acc[c] = 0;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
       const double wk = w[k];
 #pragma unroll
-      for (int c = 0; c < kChunk; ++c)
+      for (int c = 0; c < kDotChunk; ++c)
         if (c < nc) acc[c] = fma(V[(size_t)(c0 + c) * ldv + k], wk, acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < kChunk; ++c) {
+    for (int c = 0; c < kDotChunk; ++c) {
       const double v = warp_sum(acc[c]);
       if (lane == 0) sh[warp][c] = v;
     }
@@ -158,6 +158,10 @@ __global__ void b11_kernel(int n, double h, double eps, const double *__restrict
   yk[0] = y1; yk[1] = y2; yk[2] = y3;
 }
 
+__global__ void fill_u32_kernel(unsigned *__restrict__ p, unsigned v, size_t N) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) p[k] = v;
+}
+
 __global__ void to_double_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, size_t N) {
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
     if (kind == 1) y[k] = (double)reinterpret_cast<const float *>(x)[k];
@@ -209,6 +213,11 @@ cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const 
                       double *y, cudaStream_t s) {
   add_launches(1);
   b11_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
+  return cudaGetLastError();
+}
+cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s) {
+  add_launches(1);
+  fill_u32_kernel<<<grid_for(N), 256, 0, s>>>(p, v, N);
   return cudaGetLastError();
 }
 cudaError_t to_double(double *y, const void *x, int kind, size_t N, cudaStream_t s) {

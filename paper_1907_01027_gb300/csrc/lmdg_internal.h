@@ -27,8 +27,9 @@ struct SweepGeom {
   int units() const { return 4 * groups * strips; }
 };
 
-constexpr int kMaxA = 4;        // compile-time cap on angles per warp
-constexpr int kPublish = 8;     // steps between progress publications of a strip
+constexpr int kMaxA = 4;        // cap on directions per warp (template instances 1..4)
+constexpr int kChunk = 8;       // steps per chunk: cell staging, inflow staging, one CTA barrier
+constexpr unsigned kTraceEmpty = 0xFFF7FFF7u;   // 32-bit pattern of a strip trace not yet written (a NaN)
 
 // Arguments of one sweep launch (everything a kernel reads or writes).
 template <typename T>
@@ -45,9 +46,11 @@ struct SweepArgs {
   void *psi;           // storing sweep output or null (sorted->user order through perm)
   int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
   const int *perm;     // [nang] sorted index -> user index
-  T *ytr;              // [nang][strips][n][3] traces crossing strip boundaries
-  unsigned *ctrl;      // [0] ticket, [1] error, [2 + unit] progress
+  T *ytr;              // [nang][strips][n][3] traces crossing strip boundaries, kTraceEmpty when unwritten
+  unsigned *ctrl;      // [0] ticket, [1] error
   long long spin_limit;
+  const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
+  const T *cellsh;     // [nx] sigma_t h
 };
 
 // Number of kernels launched by this library (all host wrappers add to it).
@@ -57,6 +60,12 @@ void add_launches(long long k);
 // Host-side launchers (sweep.cu)
 template <typename T>
 cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s);
+template <typename T>
+size_t sweep_smem_bytes(int variant, int warps, int apw);
+template <typename T>
+int sweep_blocks_per_sm(int variant, int warps, int apw);
+// launch shape for a problem (all CTAs resident when possible); LMDG_SWEEP_GEOM="groups,warps,apw" overrides
+SweepGeom choose_geom(int variant, int n, int nq, bool fp64);
 
 // y = K x - source * b  from the partial reductions (sweep.cu)
 template <typename T>
@@ -84,8 +93,13 @@ struct lmdg_ctx {
   lmdg::SweepGeom g64{}, g32{};
   void *part = nullptr;                    // partial reductions (double-sized)
   void *ytr = nullptr;                     // inter-strip traces (double-sized)
+  void *cellsrc = nullptr;                 // [nx][4] per-sweep cell inputs (double-sized)
+  void *cellsh = nullptr;                  // [nx]
   unsigned *ctrl = nullptr;
   size_t ctrl_words = 0;
+  size_t ytr_words = 0;                    // 32-bit words of ytr
+  bool ytr_dirty = true;                   // ytr must be refilled with kTraceEmpty before the next sweep
+  int ytr_prec = -1;                       // precision (0 double, 1 float) of the last sweep using ytr
   void *psi = nullptr;                     // stored angular unknowns
   int psi_kind = -1;                       // -1 none, 0 double, 1 float, 2 bf16
   size_t psi_elems = 0;

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "lmdg_internal.h"
+#include "krylov.h"
 
 namespace lmdg {
 namespace {
@@ -38,8 +39,7 @@ __global__ void identity_kernel(int *perm, int count) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Same launch-shape rules as the context path: groups of at most 8 warps x kMaxA directions, every group
-// non-empty, every warp owning at least one direction.
+// Groups of at most 8 warps x kMaxA directions, every group non-empty (a fixed shape: no occupancy query).
 SweepGeom geom_for(int n, int nq) {
   SweepGeom g;
   g.strips = (n + 31) / 32;
@@ -48,9 +48,6 @@ SweepGeom geom_for(int n, int nq) {
   const int gsize = (nq + g.groups - 1) / g.groups;
   g.apw = (gsize + 7) / 8;
   g.warps = (gsize + g.apw - 1) / g.apw;
-  const int last = nq - (g.groups - 1) * gsize;
-  if (g.warps > last) g.warps = last;
-  g.apw = (gsize + g.warps - 1) / g.warps;
   return g;
 }
 
@@ -91,9 +88,11 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   const SweepGeom g = geom_for(n, nq);
   const size_t nx = (size_t)n * n;
   const int NR = variant == LMDG_RLM ? 6 : 4;
-  // scratch layout: [perm (kMaxDirections ints)] [control words] [partials] [strip traces]
+  // scratch layout: [perm (kMaxDirections ints)] [control words] [cell inputs] [partials] [strip traces]
   const size_t off_ctrl = align256(sizeof(int) * kMaxDirections);
-  const size_t off_part = off_ctrl + align256(sizeof(unsigned) * (2 + (size_t)g.units()));
+  const size_t off_cell = off_ctrl + align256(sizeof(unsigned) * (2 + (size_t)g.units()));
+  const size_t off_cellh = off_cell + align256(sizeof(double) * 4 * nx);
+  const size_t off_part = off_cellh + align256(sizeof(double) * nx);
   const size_t off_ytr = off_part + align256(sizeof(double) * 4 * g.groups * nx * NR);
   const size_t need = off_ytr + sizeof(double) * (size_t)n_omega * g.strips * n * 3;
   if (need > kScratchBytes) return LMDG_ERR_ARG;   // problem too large for the fixed scratch
@@ -119,7 +118,13 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   a.perm = reinterpret_cast<const int *>(base);
   a.ytr = reinterpret_cast<double *>(base + off_ytr);
   a.ctrl = reinterpret_cast<unsigned *>(base + off_ctrl);   // cleared by launch_sweep before the kernel
+  a.cellsrc = reinterpret_cast<const double *>(base + off_cell);
+  a.cellsh = reinterpret_cast<const double *>(base + off_cellh);
   a.spin_limit = spin_limit;
+  // strip traces start empty (the buffer is shared with earlier calls of any size)
+  if (fill_u32(reinterpret_cast<unsigned *>(base + off_ytr), kTraceEmpty,
+               2 * (size_t)n_omega * g.strips * n * 3, s) != cudaSuccess)
+    return LMDG_ERR_CUDA;
   if (launch_sweep<double>(variant, a, s) != cudaSuccess) return LMDG_ERR_CUDA;
   if (launch_epilogue<double>(variant, n, (int)nx, 4 * g.groups, h, a.part, x, sigma_s_over_eps, nullptr, nullptr,
                               0, y, s) != cudaSuccess)

@@ -3,14 +3,21 @@
 // angular reduction fused into the sweep.
 //
 // Work decomposition.  The mesh is cut into strips of 32 rows (in the sweep direction of a quadrant).  One
-// CTA owns one (quadrant, angle group, strip); its warps hold disjoint directions of the group.  Lane k of a
-// warp owns row k of the strip and at step t solves the cell in column t - k, so the cell below (row k-1,
-// same column) was solved by lane k-1 at step t-1 and arrives by a warp shuffle, and the cell to the left is
-// the lane's own previous result.  Lane 0 takes its inflow from the strip below through a global trace
-// buffer guarded by a per-strip progress counter; lane 31 publishes the traces for the strip above.  CTAs
-// take their (strip, quadrant, group) from an atomic ticket in strip-major order, so a CTA only ever waits for
-// a strip owned by a CTA that started earlier: the wavefront cannot deadlock whatever the residency.  Every
-// wait is bounded (spin_limit polls); on expiry the CTA raises the error word and returns.
+// CTA owns one (quadrant, angle group, strip); its warps hold disjoint directions of the group, APW each.
+// Lane k of a warp owns row k of the strip and at step t solves the cell in column t - k, so the cell below
+// (row k-1, same column) was solved by lane k-1 at step t-1 and arrives by a warp shuffle, and the cell to
+// the left is the lane's own previous result.  Steps are grouped in chunks of kChunk:
+//   - the cell data of the next chunk (source moments and sigma_t h, prepared once per sweep by
+//     prep_kernel) is copied into shared memory with cp.async while the current chunk computes;
+//   - each warp reads the chunk's inflow traces for its own directions from the strip below (prefetched
+//     during the previous chunk) and stages them in shared memory; a trace that has not been written yet
+//     still holds the empty pattern and is polled (bounded) until it arrives -- each warp depends only on
+//     the warp with the same directions in the strip below, with no flags and no fences;
+//   - per-step partial reductions go to a double-buffered shared array, and one barrier per chunk precedes
+//     a fixed-order sum over the warps.
+// CTAs take their (strip, quadrant, group) from an atomic ticket in strip-major order, so a CTA only waits
+// for a strip owned by a CTA that started earlier: the wavefront cannot deadlock whatever the residency.
+// Every wait is bounded (spin_limit polls); on expiry the CTA raises the error word and returns.
 //
 // Local coordinates.  Each quadrant is swept with the mesh mirrored so that its directions have
 // Omega_x, Omega_y > 0; a cell's Legendre coefficients transform as (u0, sx u1, sy u2, sx sy u3).  With
@@ -44,21 +51,39 @@ __device__ __forceinline__ double rcp(double x) {
 }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+// asynchronous global -> shared copies (16, 8 or 4 bytes, both addresses aligned to the size)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T> __device__ __forceinline__ void copy_cell(T *dst4, T *dsth, const T *src4, const T *srch);
+template <> __device__ __forceinline__ void copy_cell<float>(float *d4, float *dh, const float *s4, const float *sh) {
+  cp_async16(d4, s4);
+  cp_async4(dh, sh);
+}
+template <> __device__ __forceinline__ void copy_cell<double>(double *d4, double *dh, const double *s4,
+                                                             const double *sh) {
+  cp_async16(d4, s4);
+  cp_async16(d4 + 2, s4 + 2);
+  cp_async8(dh, sh);
+}
 
 template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size_t idx, T v, int bf16) {
   if (bf16) reinterpret_cast<__nv_bfloat16 *>(psi)[idx] = __float2bfloat16((float)v);
@@ -67,24 +92,95 @@ template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Strip-boundary traces carry their own readiness: the buffer holds the NaN pattern kTraceEmpty (every 32-bit
+// word 0xFFF7FFF7, never produced by arithmetic, whose NaNs are canonical) until the producing lane stores
+// the value, and the consuming warp writes the pattern back after reading it.  Aligned 32/64-bit stores are
+// single-copy atomic, so a reader sees either the pattern or the whole value.
+__device__ __forceinline__ bool is_empty(float v) { return __float_as_uint(v) == kTraceEmpty; }
+__device__ __forceinline__ bool is_empty(double v) {
+  return (unsigned long long)__double_as_longlong(v) == (((unsigned long long)kTraceEmpty << 32) | kTraceEmpty);
+}
+__device__ __forceinline__ float empty_value(float) { return __uint_as_float(kTraceEmpty); }
+__device__ __forceinline__ double empty_value(double) {
+  return __longlong_as_double((long long)(((unsigned long long)kTraceEmpty << 32) | kTraceEmpty));
+}
+__device__ __forceinline__ float ld_relaxed_t(const float *p) {
+  float v;
+  asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed_t(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+
 }  // namespace
 
-template <typename T, int VAR, bool STORE>
+// Shared-memory bytes of one CTA: partial reductions [2][kChunk][W][NR][32], cell data [2][kChunk][32][4] and
+// [2][kChunk][32], upstream traces [W][APW][kChunk][NS].
+template <typename T>
+size_t sweep_smem_bytes(int variant, int warps, int apw) {
+  const int NR = variant == LMDG_RLM ? 6 : 4, NS = variant == LMDG_RLM ? 3 : 2;
+  return sizeof(T) * ((size_t)2 * kChunk * warps * NR * 32 + (size_t)2 * kChunk * 32 * 5 +
+                      (size_t)warps * apw * kChunk * NS);
+}
+
+// Per-cell inputs of one sweep, global basis: src = 2h D_r (sigma_s/eps X_r + eps q_r) for the standard
+// scheme; (2h (sigma_s/eps X0 + eps q0), isotropic slopes -(X1 + P1 r_alpha)) for the low-memory schemes
+// (q and P1 r_alpha only in source sweeps; angle-dependent q is added inside the sweep).  sh = sigma_t h.
+template <typename T, int VAR>
+__global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, const T *__restrict__ sse,
+                            const T *__restrict__ sigt, const T *__restrict__ q, const T *__restrict__ p1ra,
+                            int source, int q_iso, T *__restrict__ src, T *__restrict__ sh) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double2 Xa = reinterpret_cast<const double2 *>(X)[2 * (size_t)K];
+  const double2 Xb = reinterpret_cast<const double2 *>(X)[2 * (size_t)K + 1];
+  const T s = sse[K];
+  T q4[4] = {0, 0, 0, 0};
+  if (source && q_iso) {
+    const T *qp = q + 4 * (size_t)K;
+    q4[0] = qp[0]; q4[1] = qp[1]; q4[2] = qp[2]; q4[3] = qp[3];
+  }
+  T o[4];
+  if (VAR == 0) {
+    o[0] = 2 * h * (s * (T)Xa.x + eps * q4[0]);
+    o[1] = (2 * h / 3) * (s * (T)Xa.y + eps * q4[1]);
+    o[2] = (2 * h / 3) * (s * (T)Xb.x + eps * q4[2]);
+    o[3] = (2 * h / 9) * (s * (T)Xb.y + eps * q4[3]);
+  } else {
+    T p1 = 0, p2 = 0;
+    if (VAR == 2 && source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; }
+    o[0] = 2 * h * (s * (T)Xa.x + eps * q4[0]);
+    o[1] = -((T)Xa.y + p1);
+    o[2] = -((T)Xb.x + p2);
+    o[3] = -(T)Xb.y;
+  }
+  T *d = src + 4 * (size_t)K;
+  d[0] = o[0]; d[1] = o[1]; d[2] = o[2]; d[3] = o[3];
+  sh[K] = sigt[K] * h;
+}
+
+template <typename T, int VAR, int APW>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
   constexpr int NR = (VAR == 2) ? 6 : 4;   // reduced values per cell
   constexpr int NS = (VAR == 2) ? 3 : 2;   // trace values passed downwind per face
+  constexpr int C = kChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *buf = reinterpret_cast<T *>(smem_raw);  // [2][W][NR][32]
   __shared__ int s_unit, s_abort;
-  __shared__ unsigned s_avail;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int W = A.g.warps;
   const int n = A.n, nx = A.nx;
+  T *red = reinterpret_cast<T *>(smem_raw);          // [2][C][W][NR][32]
+  T *cs = red + (size_t)2 * C * W * NR * 32;         // [2][C][32][4]
+  T *csh = cs + (size_t)2 * C * 32 * 4;              // [2][C][32]
+  T *yup = csh + (size_t)2 * C * 32;                 // [W][APW][C][NS]
+
   if (threadIdx.x == 0) {
     s_unit = (int)atomicAdd(&A.ctrl[0], 1u);
     s_abort = 0;
-    s_avail = 0;
   }
   __syncthreads();
   const int unit = s_unit;
@@ -99,14 +195,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
   const int g0 = grp * gsize;
   const int gcount = min(gsize, A.nq - g0);
 
-  int ang[kMaxA], uA[kMaxA];
-  T wA[kMaxA], aA[kMaxA], bA[kMaxA];
+  int ang[APW], uA[APW];
+  T wA[APW], aA[APW], bA[APW];
   int nA = 0;
 #pragma unroll
-  for (int k = 0; k < kMaxA; ++k) {
+  for (int k = 0; k < APW; ++k) {
     const int idx = warp + k * W;
     ang[k] = quad * A.nq + g0 + min(idx, gcount - 1);
-    if (k < A.g.apw && idx < gcount) nA = k + 1;
+    if (idx < gcount) nA = k + 1;
     uA[k] = A.perm[ang[k]];
     wA[k] = A.pd.w[ang[k]];
     aA[k] = fabs(A.pd.ox[ang[k]]);
@@ -116,235 +212,269 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
   const int row = strip * 32 + lane;
   const bool row_ok = row < n;
   const int j = sy > 0 ? row : n - 1 - row;
-  const T h = A.h, h2 = A.h * A.h;
+  const T h = A.h;
   const T c23 = (T)(2.0 / 3.0), c29 = (T)(2.0 / 9.0);
 
-  T xs[kMaxA][NS], ys[kMaxA][NS];
+  T xs[APW][NS], ys[APW][NS];
 #pragma unroll
-  for (int k = 0; k < kMaxA; ++k)
+  for (int k = 0; k < APW; ++k)
 #pragma unroll
     for (int c = 0; c < NS; ++c) xs[k][c] = ys[k][c] = (T)0;
 
-  const unsigned *prog_below = strip > 0 ? &A.ctrl[2 + unit - per_strip] : nullptr;
-  unsigned *prog_mine = &A.ctrl[2 + unit];
   const bool has_above = strip + 1 < A.g.strips;
-  int avail = 0;
+  // upstream trace entry of item it = (direction k, step s, component c) of the chunk starting at t0
+  constexpr int NI = (APW * C * NS + 31) / 32;
+  auto up_addr = [&](int it, int t0) -> T * {
+    if (it >= APW * C * NS) return nullptr;
+    const int k = it / (C * NS), rem = it - k * C * NS, s = rem / NS, c = rem - s * NS;
+    const int x = t0 + s;
+    if (k >= nA || x >= n) return nullptr;
+    const int ak = quad * A.nq + g0 + min(warp + k * W, gcount - 1);
+    return A.ytr + (((size_t)ak * A.g.strips + (strip - 1)) * n + x) * 3 + c;
+  };
+  T pre[NI];
+#pragma unroll
+  for (int q = 0; q < NI; ++q) pre[q] = (T)0;
+  if (strip > 0) {
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+      const T *p = up_addr(lane + 32 * q, 0);
+      if (p) pre[q] = ld_relaxed_t(p);
+    }
+  }
   const int nsteps = n + 31;
+  const int nchunks = (nsteps + C - 1) / C;
 
-  for (int t = 0; t < nsteps; ++t) {
-    // ---- inflow from the strip below must be published up to column t (block-uniform condition)
-    if (strip > 0 && t < n && t >= avail) {
-      if (threadIdx.x == 0) {
-        const unsigned need = (unsigned)min(n, t + kPublish);
-        long long spins = 0;
-        unsigned v = ld_acquire(prog_below);
-        while (v < need) {
-          if (++spins > A.spin_limit || ld_relaxed(&A.ctrl[1]) != 0u) {
-            atomicExch(&A.ctrl[1], 1u);
-            s_abort = 1;
-            break;
-          }
-          __nanosleep(128);
-          v = ld_acquire(prog_below);
-        }
-        __threadfence();
-        s_avail = v;
-      }
-      __syncthreads();
-      if (s_abort) return;
-      avail = (int)s_avail;
-    }
-
-    const int x = t - lane;
-    const bool act = row_ok && x >= 0 && x < n;
-    const int i = sx > 0 ? x : n - 1 - x;
-    const int K = act ? j * n + i : 0;
-    const bool xbnd = (x == 0);
-    const bool ybnd = (strip == 0 && lane == 0);
-
-    // ---- per-cell data shared by the warp's directions
-    T st = 0, sse = 0, s[4] = {0, 0, 0, 0}, iso[3] = {0, 0, 0};
-    if (act) {
-      st = A.pd.sigt[K] * h;
-      sse = A.pd.sse[K];
-      const double2 Xa = *reinterpret_cast<const double2 *>(A.X + 4 * (size_t)K);
-      const double2 Xb = *reinterpret_cast<const double2 *>(A.X + 4 * (size_t)K + 2);
-      const struct { double x, y, z, w; } X = {Xa.x, Xa.y, Xb.x, Xb.y};
-      T q4[4] = {0, 0, 0, 0};
-      if (A.source && !A.q_per_angle) {
-        const T *qp = A.pd.q + 4 * (size_t)K;
-        q4[0] = qp[0]; q4[1] = qp[1]; q4[2] = qp[2]; q4[3] = qp[3];
-      }
-      const T eps = A.eps;
-      if (VAR == 0) {
-        // 2h D_r (sigma_s/eps X_r + eps q_r), D = (1, 1/3, 1/3, 1/9), in local coordinates
-        s[0] = 2 * h * (sse * (T)X.x + eps * q4[0]);
-        s[1] = fsx * (2 * h / 3) * (sse * (T)X.y + eps * q4[1]);
-        s[2] = fsy * (2 * h / 3) * (sse * (T)X.z + eps * q4[2]);
-        s[3] = fsxy * (2 * h / 9) * (sse * (T)X.w + eps * q4[3]);
-      } else {
-        s[0] = 2 * h * (sse * (T)X.x + eps * q4[0]);
-        T p1 = 0, p2 = 0;
-        if (VAR == 2 && A.source && A.p1ra) {
-          p1 = A.p1ra[2 * (size_t)K];
-          p2 = A.p1ra[2 * (size_t)K + 1];
-        }
-        // isotropic slopes of the trial function: -X1 (minus P1 r_alpha in source sweeps)
-        iso[0] = -fsx * ((T)X.y + p1);
-        iso[1] = -fsy * ((T)X.z + p2);
-        iso[2] = -fsxy * (T)X.w;
+  // cell data of chunk cc -> buffer cc & 1 (item = (step, lane) of the chunk)
+  auto stage = [&](int cc) {
+    const int b = cc & 1;
+    for (int it = threadIdx.x; it < C * 32; it += blockDim.x) {
+      const int s = it >> 5, l = it & 31;
+      const int r = strip * 32 + l, x = cc * C + s - l;
+      if (r < n && x >= 0 && x < n) {
+        const int ii = sx > 0 ? x : n - 1 - x, jj = sy > 0 ? r : n - 1 - r;
+        const size_t K = (size_t)jj * n + ii;
+        copy_cell<T>(cs + ((size_t)(b * C + s) * 32 + l) * 4, csh + (size_t)(b * C + s) * 32 + l,
+                     A.cellsrc + 4 * K, A.cellsh + K);
       }
     }
+    cp_async_commit();
+  };
 
-    T acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0;
+  stage(0);
+  cp_async_wait_all();
+  __syncthreads();
 
+  for (int cc = 0; cc < nchunks; ++cc) {
+    const int t0 = cc * C;
+    const int b = cc & 1;
+    if (cc + 1 < nchunks) stage(cc + 1);
+
+    // ---- inflow from the strip below: the traces of columns [t0, t0 + C) for this warp's directions
+    // (prefetched during the previous chunk), polled until present, staged in shared memory, and consumed
+    bool wabort = false;
+    if (strip > 0 && t0 < n) {
+      int ab = 0;
+      T *yw = yup + (size_t)warp * APW * C * NS;
 #pragma unroll
-    for (int k = 0; k < kMaxA; ++k) {
-      if (k < nA) {
-        T yin[NS];
+      for (int q = 0; q < NI; ++q) {
+        const int it = lane + 32 * q;
+        T *p = up_addr(it, t0);
+        if (p) {
+          T v = pre[q];
+          long long spins = 0;
+          while (is_empty(v)) {
+            if (++spins > A.spin_limit || ld_relaxed(&A.ctrl[1]) != 0u) {
+              atomicExch(&A.ctrl[1], 1u);
+              ab = 1;
+              break;
+            }
+            __nanosleep(20);
+            v = ld_relaxed_t(p);
+          }
+          yw[it] = v;
+          *p = empty_value(v);
+        }
+      }
+      wabort = __any_sync(kFull, ab) != 0;
+      __syncwarp();
+      if (wabort && lane == 0) s_abort = 1;
+      if (!wabort && t0 + C < n) {
 #pragma unroll
-        for (int c = 0; c < NS; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
-        if (act) {
-          const int ua = uA[k];
-          if (lane == 0 && !ybnd) {
-            const T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + (strip - 1)) * n + x) * 3;
-#pragma unroll
-            for (int c = 0; c < NS; ++c) yin[c] = ldcg(yp + c);
-          }
-          const T a = aA[k], b = bA[k], wl = wA[k];
-          // inflow boundary data (local coordinates): left face side 0/1 row j, bottom face side 2/3 col i
-          T xa0 = 0, xa1 = 0, ya0 = 0, ya1 = 0;
-          if (A.source && A.pd.alpha) {
-            if (xbnd) {
-              const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sx > 0 ? 0 : 1)) * n + j) * 2);
-              xa0 = ap[0];
-              xa1 = fsy * ap[1];
-            }
-            if (ybnd) {
-              const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sy > 0 ? 2 : 3)) * n + i) * 2);
-              ya0 = ap[0];
-              ya1 = fsx * ap[1];
-            }
-          }
-          T sa[4] = {s[0], s[1], s[2], s[3]};
-          if (A.source && A.q_per_angle) {
-            const T *qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
-            const T eps = A.eps;
-            sa[0] += 2 * h * eps * qp[0];
-            if (VAR == 0) {
-              sa[1] += fsx * (2 * h / 3) * eps * qp[1];
-              sa[2] += fsy * (2 * h / 3) * eps * qp[2];
-              sa[3] += fsxy * (2 * h / 9) * eps * qp[3];
-            }
-          }
-          if (VAR == 0) {
-            // ---------------- standard Q1 block solve
-            const T U0 = xbnd ? xa0 : xs[k][0], U1 = xbnd ? xa1 : xs[k][1];
-            const T V0 = ybnd ? ya0 : yin[0], V1 = ybnd ? ya1 : yin[1];
-            const T r0 = sa[0] + 2 * a * U0 + 2 * b * V0;
-            const T r1 = sa[1] - 2 * a * U0 + c23 * b * V1;
-            const T r2 = sa[2] + c23 * a * U1 - 2 * b * V0;
-            const T r3 = sa[3] - c23 * a * U1 - c23 * b * V1;
-            const T d0 = 2 * (a + b + st);
-            const T d1 = 2 * a + c23 * (b + st);
-            const T d2 = 2 * b + c23 * (a + st);
-            const T d3 = c23 * (a + b) + c29 * st;
-            const T i1 = rcp(d1), i2 = rcp(d2);
-            const T a00 = d0 + 4 * a * a * i1 + 4 * b * b * i2;
-            const T a03 = -(T)(4.0 / 3.0) * a * b * (i1 + i2);
-            const T a33 = d3 + (T)(4.0 / 9.0) * (b * b * i1 + a * a * i2);
-            const T b0 = r0 - 2 * a * r1 * i1 - 2 * b * r2 * i2;
-            const T b3 = r3 + c23 * (b * r1 * i1 + a * r2 * i2);
-            const T idet = rcp(a00 * a33 - a03 * a03);
-            const T u0 = (a33 * b0 - a03 * b3) * idet;
-            const T u3 = (a00 * b3 - a03 * b0) * idet;
-            const T u1 = (r1 + 2 * a * u0 - c23 * b * u3) * i1;
-            const T u2 = (r2 + 2 * b * u0 - c23 * a * u3) * i2;
-            acc[0] += wl * u0;
-            acc[1] += wl * fsx * u1;
-            acc[2] += wl * fsy * u2;
-            acc[3] += wl * fsxy * u3;
-            xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
-            ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-            if (STORE) {
-              T *pp = reinterpret_cast<T *>(A.psi) + ((size_t)ua * nx + K) * 4;
-              pp[0] = u0; pp[1] = fsx * u1; pp[2] = fsy * u2; pp[3] = fsxy * u3;
-            }
-          } else {
-            // ---------------- low-memory row-0 solve (L00, or Ltilde00 with reconstruction)
-            const T U0s = xbnd ? xa0 : xs[k][0];
-            const T V0s = ybnd ? ya0 : yin[0];
-            const T d0 = 2 * (a + b + st);
-            T rhs = sa[0] + 2 * a * (U0s - iso[0]) + 2 * b * (V0s - iso[1]);
-            T u0, rec1 = 0, rec2 = 0;
-            if (VAR == 1) {
-              u0 = rhs * rcp(d0);
-            } else {
-              // reconstructed slopes (h/2) delta: interior (u0 - u0_up)/2, inflow boundary u0 - alpha_mid
-              const T cx = xbnd ? 2 * a : a, cy = ybnd ? 2 * b : b;
-              rhs += xbnd ? 2 * a * xa0 : a * xs[k][2];
-              rhs += ybnd ? 2 * b * ya0 : b * yin[2];
-              u0 = rhs * rcp(d0 + cx + cy);
-              rec1 = xbnd ? (u0 - xa0) : (T)0.5 * (u0 - xs[k][2]);
-              rec2 = ybnd ? (u0 - ya0) : (T)0.5 * (u0 - yin[2]);
-            }
-            const T u1 = iso[0] + rec1, u2 = iso[1] + rec2, u3 = iso[2];
-            // rows 1..3 of L applied to the trial function (inflow traces of L vanish on the boundary)
-            const T U0L = xbnd ? (T)0 : xs[k][0], U1L = xbnd ? (T)0 : xs[k][1];
-            const T V0L = ybnd ? (T)0 : yin[0], V1L = ybnd ? (T)0 : yin[1];
-            const T d1 = 2 * a + c23 * (b + st);
-            const T d2 = 2 * b + c23 * (a + st);
-            const T d3 = c23 * (a + b) + c29 * st;
-            const T T1 = -2 * a * u0 + d1 * u1 + c23 * b * u3 + 2 * a * U0L - c23 * b * V1L;
-            const T T2 = -2 * b * u0 + d2 * u2 + c23 * a * u3 - c23 * a * U1L + 2 * b * V0L;
-            const T T3 = -c23 * b * u1 - c23 * a * u2 + d3 * u3 + c23 * (a * U1L + b * V1L);
-            acc[0] += wl * u0;
-            acc[1] += wl * fsx * T1;
-            acc[2] += wl * fsy * T2;
-            acc[3] += wl * fsxy * T3;
-            if (VAR == 2) {
-              acc[4] += wl * fsx * rec1;
-              acc[5] += wl * fsy * rec2;
-            }
-            xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
-            ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-            if (VAR == 2) { xs[k][2] = u0; ys[k][2] = u0; }
-            if (STORE) store_psi0<T>(A.psi, (size_t)ua * nx + K, u0, A.psi_bf16);
-          }
-          if (lane == 31 && has_above) {
-            T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * 3;
-#pragma unroll
-            for (int c = 0; c < NS; ++c) yp[c] = ys[k][c];
-          }
+        for (int q = 0; q < NI; ++q) {
+          const T *p = up_addr(lane + 32 * q, t0 + C);
+          if (p) pre[q] = ld_relaxed_t(p);
         }
       }
     }
 
-    // ---- fixed-order reduction over the CTA's warps (double-buffered shared memory, one barrier a step)
-    T *bb = buf + ((size_t)((t & 1) * W + warp) * NR) * 32 + lane;
+    // ---- C steps of the diagonal pipeline
+    if (!wabort) {
+      for (int s = 0; s < C; ++s) {
+        const int t = t0 + s;
+        if (t >= nsteps) break;
+        const int x = t - lane;
+        const bool act = row_ok && x >= 0 && x < n;
+        const int i = sx > 0 ? x : n - 1 - x;
+        const int K = act ? j * n + i : 0;
+        const bool xbnd = (x == 0);
+        const bool ybnd = (strip == 0 && lane == 0);
+        // per-cell data in local coordinates
+        const T *cp4 = cs + ((size_t)(b * C + s) * 32 + lane) * 4;
+        T sl[4] = {cp4[0], cp4[1], cp4[2], cp4[3]};
+        const T st = csh[(size_t)(b * C + s) * 32 + lane];
+        sl[1] *= fsx; sl[2] *= fsy; sl[3] *= fsxy;
+
+        T acc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) bb[r * 32] = acc[r];
-    const bool publish = has_above && t >= 31 && (((t - 30) % kPublish) == 0 || t == nsteps - 1);
-    if (publish && lane == 31) __threadfence();
+        for (int r = 0; r < NR; ++r) acc[r] = 0;
+
+#pragma unroll
+        for (int k = 0; k < APW; ++k) {
+          if (k < nA) {
+            T yin[NS];
+#pragma unroll
+            for (int c = 0; c < NS; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
+            if (act) {
+              if (lane == 0 && !ybnd) {
+                const T *yw = yup + (((size_t)warp * APW + k) * C + s) * NS;
+#pragma unroll
+                for (int c = 0; c < NS; ++c) yin[c] = yw[c];
+              }
+              const T a = aA[k], bb = bA[k], wl = wA[k];
+              T xa0 = 0, xa1 = 0, ya0 = 0, ya1 = 0;
+              if (A.source && A.pd.alpha) {
+                if (xbnd) {
+                  const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sx > 0 ? 0 : 1)) * n + j) * 2);
+                  xa0 = ap[0];
+                  xa1 = fsy * ap[1];
+                }
+                if (ybnd) {
+                  const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sy > 0 ? 2 : 3)) * n + i) * 2);
+                  ya0 = ap[0];
+                  ya1 = fsx * ap[1];
+                }
+              }
+              T sa[4] = {sl[0], sl[1], sl[2], sl[3]};
+              if (A.source && A.q_per_angle) {
+                const T *qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
+                const T eps = A.eps;
+                sa[0] += 2 * h * eps * qp[0];
+                if (VAR == 0) {
+                  sa[1] += fsx * (2 * h / 3) * eps * qp[1];
+                  sa[2] += fsy * (2 * h / 3) * eps * qp[2];
+                  sa[3] += fsxy * (2 * h / 9) * eps * qp[3];
+                }
+              }
+              if (VAR == 0) {
+                // ---------------- standard Q1 block solve
+                const T U0 = xbnd ? xa0 : xs[k][0], U1 = xbnd ? xa1 : xs[k][1];
+                const T V0 = ybnd ? ya0 : yin[0], V1 = ybnd ? ya1 : yin[1];
+                const T r0 = sa[0] + 2 * a * U0 + 2 * bb * V0;
+                const T r1 = sa[1] - 2 * a * U0 + c23 * bb * V1;
+                const T r2 = sa[2] + c23 * a * U1 - 2 * bb * V0;
+                const T r3 = sa[3] - c23 * a * U1 - c23 * bb * V1;
+                const T d0 = 2 * (a + bb + st);
+                const T d1 = 2 * a + c23 * (bb + st);
+                const T d2 = 2 * bb + c23 * (a + st);
+                const T d3 = c23 * (a + bb) + c29 * st;
+                const T i1 = rcp(d1), i2 = rcp(d2);
+                const T a00 = d0 + 4 * a * a * i1 + 4 * bb * bb * i2;
+                const T a03 = -(T)(4.0 / 3.0) * a * bb * (i1 + i2);
+                const T a33 = d3 + (T)(4.0 / 9.0) * (bb * bb * i1 + a * a * i2);
+                const T b0 = r0 - 2 * a * r1 * i1 - 2 * bb * r2 * i2;
+                const T b3 = r3 + c23 * (bb * r1 * i1 + a * r2 * i2);
+                const T idet = rcp(a00 * a33 - a03 * a03);
+                const T u0 = (a33 * b0 - a03 * b3) * idet;
+                const T u3 = (a00 * b3 - a03 * b0) * idet;
+                const T u1 = (r1 + 2 * a * u0 - c23 * bb * u3) * i1;
+                const T u2 = (r2 + 2 * bb * u0 - c23 * a * u3) * i2;
+                acc[0] += wl * u0;
+                acc[1] += wl * fsx * u1;
+                acc[2] += wl * fsy * u2;
+                acc[3] += wl * fsxy * u3;
+                xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
+                ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
+                if (A.psi) {
+                  T *pp = reinterpret_cast<T *>(A.psi) + ((size_t)uA[k] * nx + K) * 4;
+                  pp[0] = u0; pp[1] = fsx * u1; pp[2] = fsy * u2; pp[3] = fsxy * u3;
+                }
+              } else {
+                // ---------------- low-memory row-0 solve (L00, or Ltilde00 with reconstruction)
+                const T U0s = xbnd ? xa0 : xs[k][0];
+                const T V0s = ybnd ? ya0 : yin[0];
+                const T d0 = 2 * (a + bb + st);
+                T rhs = sa[0] + 2 * a * (U0s - sa[1]) + 2 * bb * (V0s - sa[2]);
+                T u0, rec1 = 0, rec2 = 0;
+                if (VAR == 1) {
+                  u0 = rhs * rcp(d0);
+                } else {
+                  // reconstructed slopes (h/2) delta: interior (u0 - u0_up)/2, inflow boundary u0 - alpha_mid
+                  const T cx = xbnd ? 2 * a : a, cy = ybnd ? 2 * bb : bb;
+                  rhs += xbnd ? 2 * a * xa0 : a * xs[k][NS - 1];
+                  rhs += ybnd ? 2 * bb * ya0 : bb * yin[NS - 1];
+                  u0 = rhs * rcp(d0 + cx + cy);
+                  rec1 = xbnd ? (u0 - xa0) : (T)0.5 * (u0 - xs[k][NS - 1]);
+                  rec2 = ybnd ? (u0 - ya0) : (T)0.5 * (u0 - yin[NS - 1]);
+                }
+                const T u1 = sa[1] + rec1, u2 = sa[2] + rec2, u3 = sa[3];
+                // rows 1..3 of L applied to the trial function (inflow traces of L vanish on the boundary)
+                const T U0L = xbnd ? (T)0 : xs[k][0], U1L = xbnd ? (T)0 : xs[k][1];
+                const T V0L = ybnd ? (T)0 : yin[0], V1L = ybnd ? (T)0 : yin[1];
+                const T d1 = 2 * a + c23 * (bb + st);
+                const T d2 = 2 * bb + c23 * (a + st);
+                const T d3 = c23 * (a + bb) + c29 * st;
+                const T T1 = -2 * a * u0 + d1 * u1 + c23 * bb * u3 + 2 * a * U0L - c23 * bb * V1L;
+                const T T2 = -2 * bb * u0 + d2 * u2 + c23 * a * u3 - c23 * a * U1L + 2 * bb * V0L;
+                const T T3 = -c23 * bb * u1 - c23 * a * u2 + d3 * u3 + c23 * (a * U1L + bb * V1L);
+                acc[0] += wl * u0;
+                acc[1] += wl * fsx * T1;
+                acc[2] += wl * fsy * T2;
+                acc[3] += wl * fsxy * T3;
+                if (VAR == 2) {
+                  acc[NR - 2] += wl * fsx * rec1;
+                  acc[NR - 1] += wl * fsy * rec2;
+                }
+                xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
+                ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
+                if (VAR == 2) { xs[k][NS - 1] = u0; ys[k][NS - 1] = u0; }
+                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
+              }
+              if (lane == 31 && has_above) {
+                T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * 3;
+#pragma unroll
+                for (int c = 0; c < NS; ++c) yp[c] = ys[k][c];
+              }
+            }
+          }
+        }
+        T *rb = red + ((size_t)((b * C + s) * W + warp) * NR) * 32 + lane;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) rb[r * 32] = acc[r];
+      }
+    }
+
+    // ---- end of chunk: one barrier, then a fixed-order sum over the warps
+    cp_async_wait_all();
     __syncthreads();
-    if (warp == 0 && act) {
+    if (s_abort) return;
+    for (int it = threadIdx.x; it < C * 32; it += blockDim.x) {
+      const int s = it >> 5, l = it & 31;
+      const int t = t0 + s, x = t - l, r = strip * 32 + l;
+      if (t >= nsteps || r >= n || x < 0 || x >= n) continue;
+      const int ii = sx > 0 ? x : n - 1 - x, jj = sy > 0 ? r : n - 1 - r;
+      const size_t K = (size_t)jj * n + ii;
       T sum[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) sum[r] = 0;
+      for (int q = 0; q < NR; ++q) sum[q] = 0;
       for (int ww = 0; ww < W; ++ww) {
-        const T *src = buf + ((size_t)((t & 1) * W + ww) * NR) * 32 + lane;
+        const T *src = red + ((size_t)((b * C + s) * W + ww) * NR) * 32 + l;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) sum[r] += src[r * 32];
+        for (int q = 0; q < NR; ++q) sum[q] += src[q * 32];
       }
       T *dst = A.part + ((size_t)pq * nx + K) * NR;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) dst[r] = sum[r];
-    }
-    if (publish && threadIdx.x == 0) {
-      __threadfence();
-      st_release(prog_mine, (unsigned)min(n, t - 30));
+      for (int q = 0; q < NR; ++q) dst[q] = sum[q];
     }
   }
 }
@@ -374,10 +504,9 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   }
   const double2 xa = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K);
   const double2 xb = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K + 2);
-  const struct { double x, y, z, w; } x = {xa.x, xa.y, xb.x, xb.y};
-  struct { double x, y, z, w; } out;
+  double o0, o1, o2, o3;
   if (VAR == 0) {
-    out.x = x.x - s[0]; out.y = x.y - s[1]; out.z = x.z - s[2]; out.w = x.w - s[3];
+    o0 = xa.x - s[0]; o1 = xa.y - s[1]; o2 = xb.x - s[2]; o3 = xb.y - s[3];
   } else {
     const double m = sse[K] * h * h;
     double S1 = 0, S2 = 0;
@@ -385,37 +514,85 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
       S1 = s[4]; S2 = s[5];
       if (source && p1ra) { S1 -= p1ra[2 * (size_t)K]; S2 -= p1ra[2 * (size_t)K + 1]; }
     }
-    out.x = x.x - s[0];
-    out.y = m * (1.0 / 3.0) * (S1 - x.y) - 0.5 * h * s[1];
-    out.z = m * (1.0 / 3.0) * (S2 - x.z) - 0.5 * h * s[2];
-    out.w = m * (1.0 / 9.0) * (0.0 - x.w) - 0.5 * h * s[3];
-    if (source) { out.y += sq1[3 * (size_t)K]; out.z += sq1[3 * (size_t)K + 1]; out.w += sq1[3 * (size_t)K + 2]; }
+    o0 = xa.x - s[0];
+    o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * s[1];
+    o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * s[2];
+    o3 = m * (1.0 / 9.0) * (0.0 - xb.y) - 0.5 * h * s[3];
+    if (source) { o1 += sq1[3 * (size_t)K]; o2 += sq1[3 * (size_t)K + 1]; o3 += sq1[3 * (size_t)K + 2]; }
   }
-  *reinterpret_cast<double2 *>(y + 4 * (size_t)K) = make_double2(out.x, out.y);
-  *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(out.z, out.w);
+  *reinterpret_cast<double2 *>(y + 4 * (size_t)K) = make_double2(o0, o1);
+  *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(o2, o3);
+}
+
+template <typename T, int VAR, int APW>
+static const void *kernel_ptr() {
+  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW>);
 }
 
 template <typename T, int VAR>
-static cudaError_t launch_var(const SweepArgs<T> &a, bool store, cudaStream_t s) {
-  constexpr int NR = (VAR == 2) ? 6 : 4;
-  const size_t smem = 2ull * a.g.warps * NR * 32 * sizeof(T);
-  const dim3 grid(a.g.units()), block(a.g.warps * 32);
-  cudaError_t e = cudaMemsetAsync(a.ctrl, 0, (2 + (size_t)a.g.units()) * sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
-  add_launches(1);
-  if (store) sweep_kernel<T, VAR, true><<<grid, block, smem, s>>>(a);
-  else sweep_kernel<T, VAR, false><<<grid, block, smem, s>>>(a);
-  return cudaGetLastError();
+static const void *kernel_for(int apw) {
+  switch (apw) {
+    case 1: return kernel_ptr<T, VAR, 1>();
+    case 2: return kernel_ptr<T, VAR, 2>();
+    case 3: return kernel_ptr<T, VAR, 3>();
+    default: return kernel_ptr<T, VAR, 4>();
+  }
+}
+
+template <typename T>
+static const void *sweep_kernel_ptr(int variant, int apw) {
+  switch (variant) {
+    case LMDG_STD: return kernel_for<T, 0>(apw);
+    case LMDG_LM: return kernel_for<T, 1>(apw);
+    default: return kernel_for<T, 2>(apw);
+  }
+}
+
+template <typename T>
+int sweep_blocks_per_sm(int variant, int warps, int apw) {
+  const void *k = sweep_kernel_ptr<T>(variant, apw);
+  const size_t smem = sweep_smem_bytes<T>(variant, warps, apw);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem) != cudaSuccess) return 0;
+  return nb;
 }
 
 template <typename T>
 cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
-  const bool store = a.psi != nullptr;
-  switch (variant) {
-    case LMDG_STD: return launch_var<T, 0>(a, store, s);
-    case LMDG_LM: return launch_var<T, 1>(a, store, s);
-    default: return launch_var<T, 2>(a, store, s);
+  // per-cell inputs in the sweep's precision
+  {
+    const int bs = 256, gs = (a.nx + bs - 1) / bs;
+    add_launches(1);
+    T *src = const_cast<T *>(a.cellsrc), *sh = const_cast<T *>(a.cellsh);
+    const int qiso = a.q_per_angle ? 0 : 1;
+    switch (variant) {
+      case LMDG_STD:
+        prep_kernel<T, 0><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
+                                            qiso, src, sh);
+        break;
+      case LMDG_LM:
+        prep_kernel<T, 1><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
+                                            qiso, src, sh);
+        break;
+      default:
+        prep_kernel<T, 2><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
+                                            qiso, src, sh);
+        break;
+    }
   }
+  cudaError_t e = cudaMemsetAsync(a.ctrl, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw);
+  const size_t smem = sweep_smem_bytes<T>(variant, a.g.warps, a.g.apw);
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  SweepArgs<T> args = a;
+  void *params[] = {&args};
+  add_launches(1);
+  e = cudaLaunchKernel(k, dim3(a.g.units()), dim3(a.g.warps * 32), params, smem, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -433,6 +610,10 @@ cudaError_t launch_epilogue(int variant, int n, int nx, int P, double h, const T
   return cudaGetLastError();
 }
 
+template size_t sweep_smem_bytes<double>(int, int, int);
+template size_t sweep_smem_bytes<float>(int, int, int);
+template int sweep_blocks_per_sm<double>(int, int, int);
+template int sweep_blocks_per_sm<float>(int, int, int);
 template cudaError_t launch_sweep<double>(int, const SweepArgs<double> &, cudaStream_t);
 template cudaError_t launch_sweep<float>(int, const SweepArgs<float> &, cudaStream_t);
 template cudaError_t launch_epilogue<double>(int, int, int, int, double, const double *, const double *,
