@@ -266,3 +266,62 @@ void osw_elem_tables(double h, double *out) {
   memcpy(out + 48, e.selff, sizeof(e.selff));
   memcpy(out + 112, e.nbrf, sizeof(e.nbrf));
 }
+
+/* out = L_l^T u for one angle (transpose of the unweighted block of Appendix A).  Row block K of L^T collects
+ * the transposed diagonal block of K and the transposed coupling blocks L[K', K] of every cell K' that takes
+ * its inflow from K (the downwind neighbours of K). */
+void osw_apply_LT(int n, double h, double ox, double oy, const double *sigt, const double *u, double *out) {
+  elem_t e;
+  build_elem(h, &e);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      int K = j * n + i;
+      double A[4][4];
+      diag_block(&e, ox, oy, sigt[K], A);
+      double s[4] = {0, 0, 0, 0};
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) s[r] += A[q][r] * u[4 * K + q];
+      /* K' = neighbour across face f of K; K is K''s inflow neighbour across the opposite face g of K' */
+      for (int f = 0; f < 4; ++f) {
+        int k2 = nbr(n, i, j, f);
+        if (k2 < 0) continue;
+        int g = f ^ 1;                       /* W<->E, S<->N */
+        double on = ox * e.nrm[g][0] + oy * e.nrm[g][1];
+        if (on < 0)                          /* inflow face of K' */
+          for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < 4; ++q) s[r] += on * e.nbrf[g][q][r] * u[4 * k2 + q];
+      }
+      for (int r = 0; r < 4; ++r) out[4 * K + r] = s[r];
+    }
+}
+
+/* Solve L_l^T u = b (unweighted block) by back substitution: L_l is block lower triangular in upwind order, so
+ * its transpose is solved in the reverse order, each cell's transposed diagonal block against b minus the
+ * transposed couplings to its (already solved) downwind neighbours. */
+void osw_sweep_LT(int n, double h, double ox, double oy, const double *sigt, const double *b, double *u) {
+  elem_t e;
+  build_elem(h, &e);
+  memset(u, 0, sizeof(double) * 4 * (size_t)n * n);
+  for (int jj = n - 1; jj >= 0; --jj) {
+    int j = oy > 0 ? jj : n - 1 - jj;
+    for (int ii = n - 1; ii >= 0; --ii) {
+      int i = ox > 0 ? ii : n - 1 - ii;
+      int K = j * n + i;
+      double A[4][4], At[4][4], rhs[4];
+      diag_block(&e, ox, oy, sigt[K], A);
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) At[r][q] = A[q][r];
+      for (int r = 0; r < 4; ++r) rhs[r] = b[4 * K + r];
+      for (int f = 0; f < 4; ++f) {
+        int k2 = nbr(n, i, j, f);
+        if (k2 < 0) continue;
+        int g = f ^ 1;
+        double on = ox * e.nrm[g][0] + oy * e.nrm[g][1];
+        if (on < 0)
+          for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < 4; ++q) rhs[r] -= on * e.nbrf[g][q][r] * u[4 * k2 + q];
+      }
+      solve4(At, rhs, &u[4 * K]);
+    }
+  }
+}

@@ -251,3 +251,37 @@ def solve(p, variant):
 def operator_matrices(p):
     """(L, S, Q) of Appendix A, exposed for adjoint and invariant checks."""
     return assemble(p)
+
+
+def adjoint_std(p, g):
+    """Dense adjoint of the standard scheme: A = L - S and Q of Appendix A; A Psi = Q; J = G^T Psi with
+    G_(l,K,r) = w_l g_K int_K b_r; A^T lam = G; dJ/dp = lam^T (dQ/dp - dA/dp Psi).  A and Q are affine in each
+    sigma_s, sigma_a and q value, so dA/dp and dQ/dp are differences of two assemblies (exact up to rounding)."""
+    import copy
+    L, S, Q = assemble(p)
+    A = L - S
+    psi = np.linalg.solve(A, Q)
+    na, nx = p.nang, p.nx
+    mass = _ref_integrals(p.h)[0]
+    Gv = np.zeros(na * nx * 4)
+    for l in range(na):
+        for K in range(nx):
+            Gv[(l * nx + K) * 4:(l * nx + K) * 4 + 4] = p.w[l] * g[K] * mass[:, 0]
+    J = float(Gv @ psi)
+    lam = np.linalg.solve(A.T, Gv)
+    out = []
+    for field in ("sigma_s", "sigma_a", "q"):
+        d = np.zeros(nx)
+        for K in range(nx):
+            p2 = copy.deepcopy(p)
+            if field == "q":
+                if p2.q.ndim == 3:
+                    p2.q[:, K, 0] += 1.0
+                else:
+                    p2.q[K, 0] += 1.0
+            else:
+                getattr(p2, field)[K] += 1.0
+            L2, S2, Q2 = assemble(p2)
+            d[K] = lam @ ((Q2 - Q) - ((L2 - S2) - A) @ psi)
+        out.append(d)
+    return J, out[0], out[1], out[2]

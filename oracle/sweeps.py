@@ -38,7 +38,7 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(_build.build())
         dp = ctypes.POINTER(ctypes.c_double)
-        for name in ("osw_apply_L", "osw_sweep_L", "osw_sweep_L00", "osw_sweep_Lt00"):
+        for name in ("osw_apply_L", "osw_sweep_L", "osw_sweep_L00", "osw_sweep_Lt00", "osw_apply_LT", "osw_sweep_LT"):
             f = getattr(lib, name)
             f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
             f.restype = None
@@ -88,6 +88,14 @@ class SweepOracle:
     def Linv(self, l, b):
         """(L^-1 b)_l: solves w_l Lhat_l u = b by an upwind sweep."""
         return self._call("osw_sweep_L", l, b.ravel() / self.p.w[l], 4 * self.nx).reshape(self.nx, 4)
+
+    def LT(self, l, u):
+        """(L^T u)_l = w_l Lhat_l^T u."""
+        return self.p.w[l] * self._call("osw_apply_LT", l, u.ravel(), 4 * self.nx).reshape(self.nx, 4)
+
+    def LTinv(self, l, b):
+        """Solves w_l Lhat_l^T u = b by the reverse-order transposed sweep."""
+        return self._call("osw_sweep_LT", l, b.ravel() / self.p.w[l], 4 * self.nx).reshape(self.nx, 4)
 
     def L00inv(self, l, b0):
         return self._call("osw_sweep_L00", l, b0 / self.p.w[l], self.nx)
@@ -456,3 +464,45 @@ def _b11_sparse(so):
                       shape=(3 * nx, 3 * nx))
     A.sum_duplicates()
     return A
+
+
+def adjoint_std(so, g, tol=1e-13, direct=None):
+    """Sensitivities of J = sum_K g_K int_K psi_bar dx for the standard scheme (no paper counterpart: the
+    discrete adjoint of eq-sndg-mat).  Per direction the state satisfies Lhat_l psi_l = Mhat Phi + Qhat_l; the
+    multipliers satisfy Lhat_l^T lam_l = G + Mhat^T Lam, Lam = sum_l w_l lam_l, G_K = g_K int_K b_r (r = 0),
+    solved through the reduced system Lam - sum_l w_l Lhat_l^-T Mhat Lam = sum_l w_l Lhat_l^-T G with the
+    reverse transposed sweeps.  dJ/dp = sum_l w_l lam_l^T (dQhat_l/dp - dLhat_l/dp psi_l + dMhat/dp Phi):
+      sigma_s: dLhat = dMhat = mass/eps;  sigma_a: dLhat = eps mass;  q (cell constant): dQhat = eps mass e_0.
+    Returns (J, dJ/dsigma_s, dJ/dsigma_a, dJ/dq, lam, psi)."""
+    p = so.p
+    fwd = so.solve("std", tol=tol, direct=direct)
+    psi, Phi = fwd["psi"], fwd["phi"]
+    mass = so.mass
+    G = np.zeros((so.nx, 4))
+    G[:, 0] = g * mass[0, 0]
+    J = float(np.sum(g * (Phi @ mass.T)[:, 0]))
+    n4 = 4 * so.nx
+
+    def Kadj(v):
+        v = v.reshape(so.nx, 4)
+        acc = so._angles_sum(lambda l: p.w[l] * so.LTinv(l, p.w[l] * so.sse[:, None] * (v @ mass.T)), (so.nx, 4))
+        return (v - acc).ravel()
+    b = so._angles_sum(lambda l: p.w[l] * so.LTinv(l, p.w[l] * G), (so.nx, 4)).ravel()
+    if direct is None:
+        direct = n4 <= 1024
+    if direct:
+        Km = np.array([Kadj(e) for e in np.eye(n4)]).T
+        Lam = np.linalg.solve(Km, b).reshape(so.nx, 4)
+    else:
+        op = spla.LinearOperator((n4, n4), matvec=Kadj, dtype=np.float64)
+        Lam, _ = spla.gmres(op, b, rtol=tol, atol=0.0, restart=30, maxiter=20000)
+        Lam = Lam.reshape(so.nx, 4)
+    MLam = so.sse[:, None] * (Lam @ mass.T)
+    lam = np.stack(so._angles_map(lambda l: so.LTinv(l, p.w[l] * (G + MLam))))
+    # weighted per-cell correlations sum_l w_l lam_l^T mass psi_l and Lam^T mass Phi
+    corr = np.einsum("l,lkr,rs,lks->k", p.w, lam, mass, psi)
+    lamPhi = np.einsum("kr,rs,ks->k", Lam, mass, Phi)
+    d_ss = (lamPhi - corr) / p.eps
+    d_sa = -p.eps * corr
+    d_q = p.eps * mass[0, 0] * Lam[:, 0]
+    return J, d_ss, d_sa, d_q, lam, psi
