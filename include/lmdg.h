@@ -94,7 +94,8 @@ typedef struct {
   int refinements;     /* outer FP64 refinement steps (FP32 modes), 0 for FP64 */
   int sweeps_fp64;     /* full transport sweeps run in FP64 */
   int sweeps_fp32;     /* full transport sweeps run in FP32 */
-  double resid0;       /* ||r_0|| */
+  double resid0;       /* reference norm: ||r_0|| = ||b - K x0|| (FP64), or ||b|| from an FP32 sweep when an
+                          FP32 mode starts from zero */
   double resid;        /* final ||b - K x|| from an FP64 sweep */
   double time_ms;      /* wall time of the call (host clock) */
   double sweep_ms_fp64;/* device time inside FP64 sweep kernels (CUDA events around each launch) */
@@ -139,6 +140,9 @@ int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *strea
 
 /* Solve the reduced system with restarted GMRES (right-preconditioned, see lmdg_options.precond), then run
  * the recovery sweep (eq-sndg-final-sweep, eq-lm-step4 and its RLMDG analogue), storing the angular unknowns.
+ * FP32 modes: the first iterate comes from FP32 sweeps alone (an FP32 right-hand side and one FP32 GMRES
+ * cycle); every later step computes the residual b - K x with an FP64 sweep, runs FP32-sweep GMRES on it and
+ * updates x in FP64 (iterative refinement).  Convergence is ||b - K x|| <= tol ||b|| on FP64 residuals.
  *   x0  : initial guess [n*n][4] (NULL = zero), in the unknowns of lmdg_sweep with LMDG_SWEEP_SOURCE.
  *   x   : output [n*n][4], the converged unknowns (may be NULL).
  *   phi : output [n*n][4], the scalar-flux moments sum_l w_l psi_l of the discrete solution (may be NULL).
@@ -153,9 +157,13 @@ int lmdg_solve(lmdg_ctx *ctx, const double *x0, double *x, double *phi, lmdg_sta
 int lmdg_get_psi(lmdg_ctx *ctx, double *psi, int flags, void *stream);
 
 /* Adjoint sensitivities of the detector functional J = sum_K g_K int_K Psi_bar dx (g: [n*n] weights) with
- * respect to the per-cell sigma_s, sigma_a and the per-cell constant source q (LMDG_STD).  Solves the
- * transposed reduced system with reverse-order transposed sweeps and combines forward and adjoint angular
- * fluxes cell by cell.  Outputs [n*n] each (any may be NULL) and J. */
+ * respect to the per-cell sigma_s, sigma_a and the per-cell constant source q (no counterpart in the paper:
+ * the discrete adjoint of its schemes), for LMDG_STD and LMDG_LM with q_layout 0 or 1.  Requires a centrally
+ * symmetric quadrature (LMDG_ERR_QUAD otherwise): then the transpose of each direction's upwind block is the
+ * block of the opposite direction, so the adjoint system is the forward reduced system with the detector
+ * response as source; the forward angular flux is stored (FP64) and correlated cell by cell with the adjoint one
+ * in a final sweep.  Outputs [n*n] each (any may be NULL) and J.  RLMDG (a Petrov-Galerkin scheme whose adjoint
+ * has reconstructed test functions) returns LMDG_ERR_ARG. */
 int lmdg_adjoint(lmdg_ctx *ctx, const double *g, double *dJ_dsigma_s, double *dJ_dsigma_a,
                  double *dJ_dq, double *J, lmdg_stats *stats, int flags, void *stream);
 

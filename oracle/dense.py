@@ -285,3 +285,41 @@ def adjoint_std(p, g):
             d[K] = lam @ ((Q2 - Q) - ((L2 - S2) - A) @ psi)
         out.append(d)
     return J, out[0], out[1], out[2]
+
+
+def adjoint(p, g, variant):
+    """Dense adjoint of the standard or low-memory scheme: the discrete system is (E^T B E) c = E^T Q with E the
+    trial/test basis (identity for the standard scheme, the V_h^lm basis for LMDG); J = G^T E c with
+    G_(l,K,r) = w_l g_K int_K b_r; (E^T B E)^T mu = E^T G; dJ/dp = mu^T E^T (dQ/dp - dB/dp E c), with dB, dQ
+    differences of affine assemblies."""
+    import copy
+    L, S, Q = assemble(p)
+    B = L - S
+    na, nx = p.nang, p.nx
+    E = np.eye(na * nx * 4) if variant == "std" else lm_basis(p)
+    mass = _ref_integrals(p.h)[0]
+    Gv = np.zeros(na * nx * 4)
+    for l in range(na):
+        for K in range(nx):
+            Gv[(l * nx + K) * 4:(l * nx + K) * 4 + 4] = p.w[l] * g[K] * mass[:, 0]
+    A = E.T @ B @ E
+    c = np.linalg.solve(A, E.T @ Q)
+    psi = E @ c
+    J = float(Gv @ psi)
+    mu = np.linalg.solve(A.T, E.T @ Gv)
+    out = []
+    for field in ("sigma_s", "sigma_a", "q"):
+        dd = np.zeros(nx)
+        for K in range(nx):
+            p2 = copy.deepcopy(p)
+            if field == "q":
+                if p2.q.ndim == 3:
+                    p2.q[:, K, 0] += 1.0
+                else:
+                    p2.q[K, 0] += 1.0
+            else:
+                getattr(p2, field)[K] += 1.0
+            L2, S2, Q2 = assemble(p2)
+            dd[K] = mu @ (E.T @ ((Q2 - Q) - ((L2 - S2) - B) @ psi))
+        out.append(dd)
+    return J, out[0], out[1], out[2]

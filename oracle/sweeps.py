@@ -63,8 +63,9 @@ class SweepOracle:
     """Matrix-free block operators of one problem.  ``threads`` angles are processed concurrently; every
     angular sum is accumulated in angle order, so results do not depend on the thread count."""
 
-    def __init__(self, p, threads=None):
+    def __init__(self, p, threads=None, literal_b11=False):
         self.p = p
+        self.literal_b11 = literal_b11
         self.n, self.h, self.nx, self.na = p.n, p.h, p.nx, p.nang
         self.sigt = np.ascontiguousarray(p.sigma_s / p.eps + p.eps * p.sigma_a, dtype=np.float64)
         self.sse = p.sigma_s / p.eps
@@ -199,6 +200,8 @@ class SweepOracle:
         return self._B11
 
     def B11fast(self, X1):
+        if self.literal_b11:
+            return self.B11(X1)
         return (self.B11mat() @ X1.reshape(-1)).reshape(self.nx, 3)
 
     def B11inv(self, r, rtol=1e-15):

@@ -70,8 +70,25 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.spin_limit = c->opt.spin_limit;
   a.cellsrc = reinterpret_cast<const T *>(c->cellsrc);
   a.cellsh = reinterpret_cast<const T *>(c->cellsh);
+  a.corr = nullptr;
+  a.rev = c->rev;
+  if (c->use_adj) {
+    if constexpr (sizeof(T) == 8) a.pd.q = c->qadj64;
+    else a.pd.q = c->qadj32;
+    a.pd.alpha = nullptr;
+    a.q_per_angle = 0;
+    a.p1ra = nullptr;
+  }
+  if constexpr (sizeof(T) == 8) a.corr = c->corr;
+  a.coef = nullptr; a.ncoef = 0; a.ncls = 0; a.cls = nullptr; a.matsh = nullptr; a.mat = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    if (c->coef) {
+      a.coef = c->coef; a.ncoef = c->ncoef; a.ncls = c->ncls; a.cls = c->cls; a.matsh = c->matsh; a.mat = c->mat;
+    }
+  }
   a.psi = nullptr;
   a.psi_bf16 = 0;
+  if (c->no_store) store = false;
   if (store) {
     int kind = f64 ? 0 : (bf16 && c->variant != LMDG_STD ? 2 : 1);
     size_t per = c->variant == LMDG_STD ? 4 : 1;
@@ -105,8 +122,9 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   CK(launch_sweep<T>(c->variant, a, s));
   CK(cudaEventRecord(c->ev1, s));
   c->ev_pending = f64 ? 0 : 1;
-  CK(launch_epilogue<T>(c->variant, c->n, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->p1ra64,
-                        c->sq1, source, y, s));
+  // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
+  CK(launch_epilogue<T>(c->variant, c->n, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse,
+                        c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
   if (f64) c->sweeps64++; else c->sweeps32++;
   return 0;
 }
@@ -303,6 +321,8 @@ void lmdg_destroy(lmdg_ctx *c) {
   cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11diag);
   cudaFree(c->sigma_a); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
   cudaFree(c->cellsrc); cudaFree(c->cellsh);
+  cudaFree(c->rev); cudaFree(c->qadj64); cudaFree(c->qadj32); cudaFree(c->adj_buf);
+  cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh); cudaFree(c->coef);
   cudaFree(c->V);
   for (auto &v : c->vec) cudaFree(v);
   cudaFree(c->red);
@@ -436,9 +456,23 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     for (int r = 0; r < 3; ++r)
       bd[3 * K + r] = eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r];
 
+  // opposite direction of every sorted direction (central symmetry, needed by the adjoint)
+  std::vector<int> rev(na, 0);
+  bool rev_ok = true;
+  for (int k = 0; k < na && rev_ok; ++k) {
+    int found = -1;
+    for (int l = 0; l < na; ++l)
+      if (std::fabs(quad->ox[l] + ox[k]) <= 1e-12 && std::fabs(quad->oy[l] + oy[k]) <= 1e-12 &&
+          std::fabs(quad->w[l] - w[k]) <= 1e-14 * w[k]) { found = l; break; }
+    if (found < 0) rev_ok = false;
+    else rev[k] = found;
+  }
+  c->rev_ok = rev_ok;
   int e = 0;
-  std::vector<double> permd(perm.begin(), perm.end());
   if (cudaMalloc(&c->perm, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (cudaMalloc(&c->rev, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (cudaMemcpy(c->rev, rev.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LMDG_ERR_CUDA);
   if (cudaMemcpy(c->perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LMDG_ERR_CUDA);
   if ((e = upload(&c->d64.ox, ox)) || (e = upload(&c->d64.oy, oy)) || (e = upload(&c->d64.w, w)) ||
@@ -469,6 +503,49 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   c->ctrl_words = 2 + (size_t)std::max(c->g64.units(), c->g32.units());
   if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);
+  // FP64 element-solve coefficient tables per (material = distinct sigma_t h, direction class = distinct
+  // (|Omega_x|, |Omega_y|)); the FP64 sweeps read them instead of forming the reciprocals and Schur products
+  {
+    std::vector<double> sh(nx);
+    for (size_t K = 0; K < nx; ++K) sh[K] = sigt[K] * h;
+    std::vector<double> uniq(sh);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<int> matv(nx);
+    for (size_t K = 0; K < nx; ++K)
+      matv[K] = (int)(std::lower_bound(uniq.begin(), uniq.end(), sh[K]) - uniq.begin());
+    std::vector<double> cab;
+    std::vector<int> clsv(na);
+    for (int k = 0; k < na; ++k) {
+      const double aa = std::fabs(ox[k]), bb = std::fabs(oy[k]);
+      int f = -1;
+      for (size_t q = 0; q < cab.size() / 2; ++q)
+        if (cab[2 * q] == aa && cab[2 * q + 1] == bb) { f = (int)q; break; }
+      if (f < 0) { f = (int)(cab.size() / 2); cab.push_back(aa); cab.push_back(bb); }
+      clsv[k] = f;
+    }
+    c->nmat = (int)uniq.size();
+    c->ncls = (int)(cab.size() / 2);
+    c->ncoef = coef_count(variant);
+    const size_t tbytes = sizeof(double) * (size_t)c->nmat * c->ncls * c->ncoef;
+    double *cabd = nullptr;
+    bool ok = cudaMalloc(&c->coef, tbytes) == cudaSuccess && cudaMalloc(&c->mat, sizeof(int) * nx) == cudaSuccess &&
+              cudaMalloc(&c->cls, sizeof(int) * na) == cudaSuccess &&
+              cudaMalloc(&c->matsh, sizeof(double) * c->nmat) == cudaSuccess &&
+              cudaMalloc(&cabd, sizeof(double) * cab.size()) == cudaSuccess;
+    ok = ok && cudaMemcpy(c->mat, matv.data(), sizeof(int) * nx, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->cls, clsv.data(), sizeof(int) * na, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->matsh, uniq.data(), sizeof(double) * c->nmat, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(cabd, cab.data(), sizeof(double) * cab.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         build_coef_tables(variant, c->nmat, c->ncls, c->matsh, cabd, c->coef, 0) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+    cudaFree(cabd);
+    if (!ok) {   // no tables: the FP64 sweeps compute the coefficients themselves
+      cudaGetLastError();
+      cudaFree(c->coef); cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh);
+      c->coef = nullptr; c->mat = nullptr; c->cls = nullptr; c->matsh = nullptr;
+    }
+  }
   *out = c;
   return 0;
 }
@@ -537,11 +614,32 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     return norm2(c, R, rn2, s);
   };
   double rn2 = 0;
-  if (int e = residual(&rn2)) return e;
-  const double r0 = std::sqrt(rn2);
-  if (!std::isfinite(r0)) return LMDG_ERR_BREAKDOWN;
-  double rn = r0;
   int iters = 0, refine = 0, status = 0;
+  double r0 = 0;
+  if (fp32 && !x0) {
+    // FP32 start: b from an FP32 source sweep (||b|| is the tolerance reference) and an FP32 GMRES cycle for
+    // the first iterate, so that the FP64 sweeps are spent only on residuals at iterates
+    if (int e = sweep_prec(c, 1, X, R, 1, false, 0, s)) return e;   // X = 0: R = K 0 - b = -b
+    CK(axpby(R, -1.0, R, 0.0, N, s));
+    if (int e = check_error_word(c, s)) return e;
+    if (int e = norm2(c, R, &rn2, s)) return e;
+    r0 = std::sqrt(rn2);
+    if (!std::isfinite(r0)) return LMDG_ERR_BREAKDOWN;
+    if (r0 > 0) {
+      GmresOut go;
+      const double target = std::max(c->opt.inner_tol * r0, 0.5 * c->opt.tol * r0);
+      if (int e = gmres_cycle(c, 1, R, r0, D, m, target, c->opt.max_iters, &go, s)) return e;
+      iters += go.iters;
+      CK(axpby(X, 1.0, D, 1.0, N, s));
+    }
+    if (int e = residual(&rn2)) return e;
+  } else {
+    if (int e = residual(&rn2)) return e;
+    r0 = std::sqrt(rn2);
+  }
+  if (!std::isfinite(r0)) return LMDG_ERR_BREAKDOWN;
+  double rn = std::sqrt(rn2);
+  if (!std::isfinite(rn)) return LMDG_ERR_BREAKDOWN;
   while (rn > c->opt.tol * r0) {
     if (iters >= c->opt.max_iters || (fp32 && refine >= c->opt.max_refine)) { status = LMDG_ERR_NOTCONV; break; }
     const double target = fp32 ? std::max(c->opt.inner_tol * rn, 0.5 * c->opt.tol * r0) : c->opt.tol * r0;
@@ -660,9 +758,79 @@ int lmdg_b11_solve(lmdg_ctx *c, const double *r, double *z, double tol, int *ite
 
 int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double *dq, double *J, lmdg_stats *st,
                  int flags, void *stream) {
-  (void)g; (void)dss; (void)dsa; (void)dq; (void)J; (void)st; (void)flags; (void)stream;
-  if (!c) return LMDG_ERR_ARG;
-  return LMDG_ERR_STATE;
+  if (!c || !g) return LMDG_ERR_ARG;
+  if (c->variant == LMDG_RLM || c->q_layout == 2) return LMDG_ERR_ARG;
+  if (!c->rev_ok) return LMDG_ERR_QUAD;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const size_t nx = (size_t)c->nx, N = 4 * nx;
+  const bool host = (flags & LMDG_HOST_PTRS) != 0;
+  if (!c->adj_buf) {
+    if (cudaMalloc(&c->adj_buf, sizeof(double) * (5 * N + 4 * nx)) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (cudaMalloc(&c->qadj64, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (cudaMalloc(&c->qadj32, sizeof(float) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+  }
+  double *Xf = c->adj_buf, *Lam = c->adj_buf + N, *Y = c->adj_buf + 2 * N, *G = c->adj_buf + 3 * N;
+  double *PhiF = c->adj_buf + 3 * N + 4 * nx, *PhiA = PhiF + N;   // scalar-flux moments (low-memory)
+  // detector source: eps h^2 q_adj = g h^2  ->  q_adj = g / eps on the cell-average moment
+  std::vector<double> qa(N, 0.0), gh(nx);
+  if (host) std::memcpy(gh.data(), g, sizeof(double) * nx);
+  else CK(cudaMemcpy(gh.data(), g, sizeof(double) * nx, cudaMemcpyDeviceToHost));
+  for (size_t K = 0; K < nx; ++K) qa[4 * K] = gh[K] / c->eps;
+  std::vector<float> qa32(qa.begin(), qa.end());
+  CK(cudaMemcpyAsync(c->qadj64, qa.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->qadj32, qa32.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(G, gh.data(), sizeof(double) * nx, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  lmdg_stats s1{}, s2{};
+  // 1. forward solve and the forward angular flux in FP64
+  c->use_adj = false; c->no_store = false;
+  int st1 = lmdg_solve(c, nullptr, Xf, PhiF, &s1, 0, stream);
+  if (st1 != 0 && st1 != LMDG_ERR_NOTCONV) return st1;
+  if (c->psi_kind != 0)
+    if (int e = do_sweep<double>(c, Xf, Y, 1, true, 0, s)) return e;
+  // 2. adjoint solve: for a centrally symmetric quadrature Lhat_l^T = Lhat_{-l} and S is symmetric, so with angle
+  //    reversal Pi, B^T = Pi B Pi; the standard and V_h^lm bases are closed under Pi, hence the adjoint system is the
+  //    forward one with the directions reversed and the detector response g as an isotropic source
+  c->use_adj = true; c->no_store = true;
+  int st2 = lmdg_solve(c, nullptr, Lam, PhiA, &s2, 0, stream);
+  if (st2 != 0 && st2 != LMDG_ERR_NOTCONV) { c->use_adj = false; c->no_store = false; return st2; }
+  // 3. correlation sweep at the multiplier: per cell sum_l w_l lam_l,r psi_l,r (lam_l = psi_adj of -Omega_l;
+  //    cell averages only for the low-memory scheme, whose slopes are isotropic)
+  c->corr = reinterpret_cast<const double *>(c->psi);
+  int e3 = do_sweep<double>(c, Lam, Y, 1, false, 0, s);
+  c->corr = nullptr; c->use_adj = false; c->no_store = false;
+  if (e3) return e3;
+  if (int e = check_error_word(c, s)) return e;
+  // 4. per-cell gradients
+  double *out = Y;   // [3][nx] reuse of the scratch vector (4 nx doubles)
+  const bool lowmem = c->variant != LMDG_STD;
+  CK(lmdg::adjoint_gradients(c->variant, c->nx, 4 * c->g64.groups, c->h, c->eps,
+                             reinterpret_cast<const double *>(c->part), lowmem ? PhiF : Xf, lowmem ? PhiA : Lam, out,
+                             s));
+  std::vector<double> xf_h(N);
+  CK(cudaMemcpyAsync(xf_h.data(), lowmem ? PhiF : Xf, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  double *dsts[3] = {dss, dsa, dq};
+  for (int f = 0; f < 3; ++f)
+    if (dsts[f]) CK(cudaMemcpyAsync(dsts[f], out + f * nx, sizeof(double) * nx,
+                                    host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (J) {
+    double acc = 0;
+    for (size_t K = 0; K < nx; ++K) acc += gh[K] * c->h * c->h * xf_h[4 * K];
+    *J = acc;
+  }
+  if (st) {
+    *st = s1;
+    st->iters += s2.iters;
+    st->refinements += s2.refinements;
+    st->sweeps_fp64 = s1.sweeps_fp64 + s2.sweeps_fp64 + 1 + (c->opt.precision != LMDG_FP64 ? 1 : 0);
+    st->sweeps_fp32 = s1.sweeps_fp32 + s2.sweeps_fp32;
+    st->resid = std::max(s1.resid / std::max(s1.resid0, 1e-300), s2.resid / std::max(s2.resid0, 1e-300));
+    st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return (st1 == LMDG_ERR_NOTCONV || st2 == LMDG_ERR_NOTCONV) ? LMDG_ERR_NOTCONV : 0;
 }
 
 }  // extern "C"

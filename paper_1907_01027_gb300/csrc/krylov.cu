@@ -158,6 +158,47 @@ __global__ void b11_kernel(int n, double h, double eps, const double *__restrict
   yk[0] = y1; yk[1] = y2; yk[2] = y3;
 }
 
+// Per-cell sensitivities of the standard scheme from the correlation partials C_r = sum_l w_l lam_l,r psi_l,r,
+// the forward scalar flux Phi and the multiplier Lam (mass = h^2 diag(1, 1/3, 1/3, 1/9)):
+//   dJ/dsigma_s = (Lam^T mass Phi - sum_r mass_r C_r) / eps,  dJ/dsigma_a = -eps sum_r mass_r C_r,
+//   dJ/dq = eps mass_0 Lam_0.
+__global__ void adjoint_grad_kernel(int nx, int P, double h, double eps, const double *__restrict__ part,
+                                    const double *__restrict__ Phi, const double *__restrict__ Lam,
+                                    double *__restrict__ out) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double D[4] = {1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
+  double corr = 0, lp = 0;
+  for (int r = 0; r < 4; ++r) {
+    double c = 0;
+    for (int p = 0; p < P; ++p) c += part[((size_t)p * nx + K) * 4 + r];
+    corr += h * h * D[r] * c;
+    lp += h * h * D[r] * Lam[4 * (size_t)K + r] * Phi[4 * (size_t)K + r];
+  }
+  out[K] = (lp - corr) / eps;
+  out[nx + K] = -eps * corr;
+  out[2 * (size_t)nx + K] = eps * h * h * Lam[4 * (size_t)K];
+}
+
+// Low-memory scheme (V_h^lm trial = test space): with the forward scalar-flux moments Phi = (X0, Phi1), the
+// adjoint solution's moments A = (Lam0, mu1) and C0 = sum_l w_l mu0_l psi0_l (correlation partials, r = 0):
+//   dJ/dsigma_s = h^2 (Lam0 X0 - C0) / eps,  dJ/dsigma_a = -eps h^2 (C0 + sum_{r>=1} D_r mu1_r Phi1_r),
+//   dJ/dq = eps h^2 Lam0   (the isotropic slope terms of dJ/dsigma_s cancel).
+__global__ void adjoint_grad_lm_kernel(int nx, int P, double h, double eps, const double *__restrict__ part,
+                                       const double *__restrict__ Phi, const double *__restrict__ Adj,
+                                       double *__restrict__ out) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  double c0 = 0;
+  for (int p = 0; p < P; ++p) c0 += part[((size_t)p * nx + K) * 4];
+  const double *f = Phi + 4 * (size_t)K, *a = Adj + 4 * (size_t)K;
+  const double h2 = h * h;
+  const double slopes = (a[1] * f[1] + a[2] * f[2]) / 3.0 + a[3] * f[3] / 9.0;
+  out[K] = h2 * (a[0] * f[0] - c0) / eps;
+  out[nx + K] = -eps * h2 * (c0 + slopes);
+  out[2 * (size_t)nx + K] = eps * h2 * a[0];
+}
+
 __global__ void fill_u32_kernel(unsigned *__restrict__ p, unsigned v, size_t N) {
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) p[k] = v;
 }
@@ -213,6 +254,13 @@ cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const 
                       double *y, cudaStream_t s) {
   add_launches(1);
   b11_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
+  return cudaGetLastError();
+}
+cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, const double *part,
+                              const double *Phi, const double *Lam, double *out, cudaStream_t s) {
+  add_launches(1);
+  if (variant == LMDG_STD) adjoint_grad_kernel<<<(nx + 255) / 256, 256, 0, s>>>(nx, P, h, eps, part, Phi, Lam, out);
+  else adjoint_grad_lm_kernel<<<(nx + 255) / 256, 256, 0, s>>>(nx, P, h, eps, part, Phi, Lam, out);
   return cudaGetLastError();
 }
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s) {

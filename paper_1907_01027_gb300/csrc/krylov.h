@@ -19,6 +19,10 @@ cudaError_t precond(double *y, const double *x, const double *diag, int nx, int 
 // y = B11 u on [nx][3]; A4 = {Ax+, Ax-, Ay+, Ay-}
 cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
                       double *y, cudaStream_t s);
+// out[0..nx) = dJ/dsigma_s, out[nx..2nx) = dJ/dsigma_a, out[2nx..3nx) = dJ/dq; Phi, Lam: forward and adjoint
+// reduced solutions (standard) or scalar-flux moments (low-memory)
+cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, const double *part,
+                              const double *Phi, const double *Lam, double *out, cudaStream_t s);
 // p[0..N) = v
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s);
 // y = (double) x, kind 0 double, 1 float, 2 bfloat16

@@ -28,7 +28,10 @@ struct SweepGeom {
 };
 
 constexpr int kMaxA = 4;        // cap on directions per warp (template instances 1..4)
-constexpr int kChunk = 8;       // steps per chunk: cell staging, inflow staging, one CTA barrier
+#ifndef LMDG_CHUNK
+#define LMDG_CHUNK 8
+#endif
+constexpr int kChunk = LMDG_CHUNK;   // steps per chunk: cell staging, inflow staging, one CTA barrier
 constexpr unsigned kTraceEmpty = 0xFFF7FFF7u;   // 32-bit pattern of a strip trace not yet written (a NaN)
 
 // Arguments of one sweep launch (everything a kernel reads or writes).
@@ -51,11 +54,27 @@ struct SweepArgs {
   long long spin_limit;
   const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
   const T *cellsh;     // [nx] sigma_t h
+  const double *corr;  // adjoint correlation mode: stored forward psi ([nang(user)][nx][4] standard, [nang][nx]
+                       // low-memory); the reduction becomes sum_l w_l u_l,r psi_rev(l),r (r = 0 only for LMDG)
+  const int *rev;      // [nang] sorted index -> user index of the opposite direction (corr mode)
+  // FP64 coefficient tables (null: coefficients computed in the kernel).  With them, cellsh carries the cell's
+  // material index and coef[(material * ncls + class) * ncoef + c] the solve coefficients of that material
+  // (sigma_t h) and direction class (|Omega_x|, |Omega_y|).
+  const double *coef;
+  int ncoef, ncls;
+  const int *cls;      // [nang] sorted index -> direction class
+  const double *matsh; // [materials] sigma_t h of each material
+  const int *mat;      // [nx] material of each cell (prep_kernel writes it into the cellsh slot)
 };
 
 // Number of kernels launched by this library (all host wrappers add to it).
 long long launch_count();
 void add_launches(long long k);
+
+// FP64 coefficient tables of the element solves (sweep.cu)
+cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *matsh, const double *cls_ab,
+                              double *coef, cudaStream_t s);
+int coef_count(int variant);
 
 // Host-side launchers (sweep.cu)
 template <typename T>
@@ -114,4 +133,19 @@ struct lmdg_ctx {
   double sweep_ms[2] = {0, 0};             // device time in FP64 / FP32 sweep kernels
   long long launches = 0;
   int sweeps64 = 0, sweeps32 = 0;
+  // adjoint (standard scheme): opposite directions, detector source, solve-time switches
+  int *rev = nullptr;                      // device [nang] sorted -> user index of -Omega
+  bool rev_ok = false;                     // the quadrature is centrally symmetric
+  double *qadj64 = nullptr;                // [nx][4] detector source g/eps (r = 0)
+  float *qadj32 = nullptr;
+  double *adj_buf = nullptr;               // [3][N] forward solution, multiplier, scratch
+  bool use_adj = false;                    // sweeps take the detector source and vacuum inflow
+  bool no_store = false;                   // solve keeps the stored psi untouched
+  const double *corr = nullptr;            // correlation sweep input (forward psi, double)
+  // FP64 coefficient tables
+  int nmat = 0, ncls = 0, ncoef = 0;
+  int *mat = nullptr;                      // [nx] material index
+  int *cls = nullptr;                      // [nang] sorted index -> direction class
+  double *matsh = nullptr;                 // [nmat] sigma_t h
+  double *coef = nullptr;                  // [nmat][ncls][ncoef]
 };

@@ -132,7 +132,8 @@ size_t sweep_smem_bytes(int variant, int warps, int apw) {
 template <typename T, int VAR>
 __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, const T *__restrict__ sse,
                             const T *__restrict__ sigt, const T *__restrict__ q, const T *__restrict__ p1ra,
-                            int source, int q_iso, T *__restrict__ src, T *__restrict__ sh) {
+                            int source, int q_iso, T *__restrict__ src, T *__restrict__ sh,
+                            const int *__restrict__ mat) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   const double2 Xa = reinterpret_cast<const double2 *>(X)[2 * (size_t)K];
@@ -159,14 +160,62 @@ __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, co
   }
   T *d = src + 4 * (size_t)K;
   d[0] = o[0]; d[1] = o[1]; d[2] = o[2]; d[3] = o[3];
-  sh[K] = sigt[K] * h;
+  sh[K] = mat ? (T)mat[K] : sigt[K] * h;
 }
 
+// Coefficients of the element solves for one material (s = sigma_t h) and one direction class (a, b) =
+// (|Omega_x|, |Omega_y|), in the local frame of the kernel:
+//   standard: i1 = 1/d1, i2 = 1/d2, p1 = 2a i1, p2 = 2b i2, q1 = 2/3 b i1, q2 = 2/3 a i2, and with the 2x2 Schur
+//             system (a00 a03; a03 a33) of the (u0, u3) unknowns, c0 = a33/det, c1 = a03/det, c3 = a00/det;
+//   low-memory: 1/d0 (LMDG) or 1/(d0 + a + b) (RLMDG interior cells), d1, d2, d3.
+int coef_count(int variant) { return variant == LMDG_STD ? 9 : 4; }
+
+__global__ void coef_kernel(int variant, int nmat, int ncls, const double *__restrict__ matsh,
+                            const double *__restrict__ cls_ab, double *__restrict__ coef) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nmat * ncls) return;
+  const int m = id / ncls, c = id - m * ncls;
+  const double s = matsh[m], a = cls_ab[2 * c], b = cls_ab[2 * c + 1];
+  const double c23 = 2.0 / 3.0, c29 = 2.0 / 9.0;
+  const double d0 = 2 * (a + b + s), d1 = 2 * a + c23 * (b + s), d2 = 2 * b + c23 * (a + s), d3 = c23 * (a + b) + c29 * s;
+  if (variant == LMDG_STD) {
+    double *o = coef + (size_t)id * 9;
+    const double i1 = 1.0 / d1, i2 = 1.0 / d2;
+    const double a00 = d0 + 4 * a * a * i1 + 4 * b * b * i2;
+    const double a03 = -(4.0 / 3.0) * a * b * (i1 + i2);
+    const double a33 = d3 + (4.0 / 9.0) * (b * b * i1 + a * a * i2);
+    const double det = a00 * a33 - a03 * a03;
+    o[0] = i1; o[1] = i2; o[2] = 2 * a * i1; o[3] = 2 * b * i2; o[4] = c23 * b * i1; o[5] = c23 * a * i2;
+    o[6] = a33 / det; o[7] = a03 / det; o[8] = a00 / det;
+  } else {
+    double *o = coef + (size_t)id * 4;
+    o[0] = variant == LMDG_LM ? 1.0 / d0 : 1.0 / (d0 + a + b);
+    o[1] = d1; o[2] = d2; o[3] = d3;
+  }
+}
+
+cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *matsh, const double *cls_ab,
+                              double *coef, cudaStream_t s) {
+  const int tot = nmat * ncls;
+  add_launches(1);
+  coef_kernel<<<(tot + 255) / 256, 256, 0, s>>>(variant, nmat, ncls, matsh, cls_ab, coef);
+  return cudaGetLastError();
+}
+
+// Minimum resident CTAs per SM requested from the compiler for the FP32 instances (register budget).
+#ifndef LMDG_MINB32
+#define LMDG_MINB32 2
+#endif
+
 template <typename T, int VAR, int APW>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr int NR = (VAR == 2) ? 6 : 4;   // reduced values per cell
   constexpr int NS = (VAR == 2) ? 3 : 2;   // trace values passed downwind per face
   constexpr int C = kChunk;
+  // coefficient tables and the adjoint correlation exist for the FP64 instances only (compiled out of FP32)
+  constexpr bool kF64 = sizeof(T) == 8;
+  const bool use_tab = kF64 && A.coef != nullptr;
+  const bool use_corr = kF64 && A.corr != nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit, s_abort;
 
@@ -195,7 +244,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
   const int g0 = grp * gsize;
   const int gcount = min(gsize, A.nq - g0);
 
-  int ang[APW], uA[APW];
+  int ang[APW], uA[APW], cA[APW], kA[APW];
   T wA[APW], aA[APW], bA[APW];
   int nA = 0;
 #pragma unroll
@@ -204,6 +253,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
     ang[k] = quad * A.nq + g0 + min(idx, gcount - 1);
     if (idx < gcount) nA = k + 1;
     uA[k] = A.perm[ang[k]];
+    cA[k] = (kF64 && A.corr) ? A.rev[ang[k]] : 0;
+    kA[k] = (kF64 && A.coef) ? A.cls[ang[k]] : 0;
     wA[k] = A.pd.w[ang[k]];
     aA[k] = fabs(A.pd.ox[ang[k]]);
     bA[k] = fabs(A.pd.oy[ang[k]]);
@@ -310,6 +361,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
 
     // ---- C steps of the diagonal pipeline
     if (!wabort) {
+#ifdef LMDG_STEP_UNROLL
+#pragma unroll LMDG_STEP_UNROLL
+#endif
       for (int s = 0; s < C; ++s) {
         const int t = t0 + s;
         if (t >= nsteps) break;
@@ -374,25 +428,50 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
                 const T r1 = sa[1] - 2 * a * U0 + c23 * bb * V1;
                 const T r2 = sa[2] + c23 * a * U1 - 2 * bb * V0;
                 const T r3 = sa[3] - c23 * a * U1 - c23 * bb * V1;
-                const T d0 = 2 * (a + bb + st);
-                const T d1 = 2 * a + c23 * (bb + st);
-                const T d2 = 2 * bb + c23 * (a + st);
-                const T d3 = c23 * (a + bb) + c29 * st;
-                const T i1 = rcp(d1), i2 = rcp(d2);
-                const T a00 = d0 + 4 * a * a * i1 + 4 * bb * bb * i2;
-                const T a03 = -(T)(4.0 / 3.0) * a * bb * (i1 + i2);
-                const T a33 = d3 + (T)(4.0 / 9.0) * (bb * bb * i1 + a * a * i2);
-                const T b0 = r0 - 2 * a * r1 * i1 - 2 * bb * r2 * i2;
-                const T b3 = r3 + c23 * (bb * r1 * i1 + a * r2 * i2);
-                const T idet = rcp(a00 * a33 - a03 * a03);
-                const T u0 = (a33 * b0 - a03 * b3) * idet;
-                const T u3 = (a00 * b3 - a03 * b0) * idet;
-                const T u1 = (r1 + 2 * a * u0 - c23 * bb * u3) * i1;
-                const T u2 = (r2 + 2 * bb * u0 - c23 * a * u3) * i2;
-                acc[0] += wl * u0;
-                acc[1] += wl * fsx * u1;
-                acc[2] += wl * fsy * u2;
-                acc[3] += wl * fsxy * u3;
+                T u0, u1, u2, u3;
+                if (use_tab) {
+                  // table: the material index travels in the staged sigma_t h slot
+                  const double *cf = A.coef + ((size_t)(int)st * A.ncls + kA[k]) * 9;
+                  const T i1 = (T)__ldg(cf), i2 = (T)__ldg(cf + 1), p1 = (T)__ldg(cf + 2), p2 = (T)__ldg(cf + 3);
+                  const T q1 = (T)__ldg(cf + 4), q2 = (T)__ldg(cf + 5), e0 = (T)__ldg(cf + 6), e1 = (T)__ldg(cf + 7);
+                  const T e3 = (T)__ldg(cf + 8);
+                  const T b0 = r0 - p1 * r1 - p2 * r2;
+                  const T b3 = r3 + q1 * r1 + q2 * r2;
+                  u0 = e0 * b0 - e1 * b3;
+                  u3 = e3 * b3 - e1 * b0;
+                  u1 = i1 * r1 + p1 * u0 - q1 * u3;
+                  u2 = i2 * r2 + p2 * u0 - q2 * u3;
+                } else {
+                  const T d0 = 2 * (a + bb + st);
+                  const T d1 = 2 * a + c23 * (bb + st);
+                  const T d2 = 2 * bb + c23 * (a + st);
+                  const T d3 = c23 * (a + bb) + c29 * st;
+                  const T i1 = rcp(d1), i2 = rcp(d2);
+                  const T a00 = d0 + 4 * a * a * i1 + 4 * bb * bb * i2;
+                  const T a03 = -(T)(4.0 / 3.0) * a * bb * (i1 + i2);
+                  const T a33 = d3 + (T)(4.0 / 9.0) * (bb * bb * i1 + a * a * i2);
+                  const T b0 = r0 - 2 * a * r1 * i1 - 2 * bb * r2 * i2;
+                  const T b3 = r3 + c23 * (bb * r1 * i1 + a * r2 * i2);
+                  const T idet = rcp(a00 * a33 - a03 * a03);
+                  u0 = (a33 * b0 - a03 * b3) * idet;
+                  u3 = (a00 * b3 - a03 * b0) * idet;
+                  u1 = (r1 + 2 * a * u0 - c23 * bb * u3) * i1;
+                  u2 = (r2 + 2 * bb * u0 - c23 * a * u3) * i2;
+                }
+                if (use_corr) {
+                  // adjoint correlation: this sweep's psi (the multiplier of the opposite direction) times the
+                  // stored forward psi of that opposite direction, per Legendre moment
+                  const double *pf = A.corr + ((size_t)cA[k] * nx + K) * 4;
+                  acc[0] += wl * u0 * (T)pf[0];
+                  acc[1] += wl * fsx * u1 * (T)pf[1];
+                  acc[2] += wl * fsy * u2 * (T)pf[2];
+                  acc[3] += wl * fsxy * u3 * (T)pf[3];
+                } else {
+                  acc[0] += wl * u0;
+                  acc[1] += wl * fsx * u1;
+                  acc[2] += wl * fsy * u2;
+                  acc[3] += wl * fsxy * u3;
+                }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
                 if (A.psi) {
@@ -403,17 +482,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
                 // ---------------- low-memory row-0 solve (L00, or Ltilde00 with reconstruction)
                 const T U0s = xbnd ? xa0 : xs[k][0];
                 const T V0s = ybnd ? ya0 : yin[0];
-                const T d0 = 2 * (a + bb + st);
+                // sigma_t h and the coefficient row (table mode: st is the material index)
+                T sh = st, inv = 0, d1, d2, d3;
+                if (use_tab) {
+                  const double *cf = A.coef + ((size_t)(int)st * A.ncls + kA[k]) * 4;
+                  inv = (T)__ldg(cf); d1 = (T)__ldg(cf + 1); d2 = (T)__ldg(cf + 2); d3 = (T)__ldg(cf + 3);
+                  sh = (T)__ldg(A.matsh + (int)st);
+                } else {
+                  d1 = 2 * a + c23 * (bb + sh);
+                  d2 = 2 * bb + c23 * (a + sh);
+                  d3 = c23 * (a + bb) + c29 * sh;
+                }
+                const T d0 = 2 * (a + bb + sh);
                 T rhs = sa[0] + 2 * a * (U0s - sa[1]) + 2 * bb * (V0s - sa[2]);
                 T u0, rec1 = 0, rec2 = 0;
                 if (VAR == 1) {
-                  u0 = rhs * rcp(d0);
+                  u0 = rhs * (use_tab ? inv : rcp(d0));
                 } else {
                   // reconstructed slopes (h/2) delta: interior (u0 - u0_up)/2, inflow boundary u0 - alpha_mid
                   const T cx = xbnd ? 2 * a : a, cy = ybnd ? 2 * bb : bb;
                   rhs += xbnd ? 2 * a * xa0 : a * xs[k][NS - 1];
                   rhs += ybnd ? 2 * bb * ya0 : bb * yin[NS - 1];
-                  u0 = rhs * rcp(d0 + cx + cy);
+                  u0 = rhs * ((use_tab && !xbnd && !ybnd) ? inv : rcp(d0 + cx + cy));
                   rec1 = xbnd ? (u0 - xa0) : (T)0.5 * (u0 - xs[k][NS - 1]);
                   rec2 = ybnd ? (u0 - ya0) : (T)0.5 * (u0 - yin[NS - 1]);
                 }
@@ -421,16 +511,19 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A) {
                 // rows 1..3 of L applied to the trial function (inflow traces of L vanish on the boundary)
                 const T U0L = xbnd ? (T)0 : xs[k][0], U1L = xbnd ? (T)0 : xs[k][1];
                 const T V0L = ybnd ? (T)0 : yin[0], V1L = ybnd ? (T)0 : yin[1];
-                const T d1 = 2 * a + c23 * (bb + st);
-                const T d2 = 2 * bb + c23 * (a + st);
-                const T d3 = c23 * (a + bb) + c29 * st;
                 const T T1 = -2 * a * u0 + d1 * u1 + c23 * bb * u3 + 2 * a * U0L - c23 * bb * V1L;
                 const T T2 = -2 * bb * u0 + d2 * u2 + c23 * a * u3 - c23 * a * U1L + 2 * bb * V0L;
                 const T T3 = -c23 * bb * u1 - c23 * a * u2 + d3 * u3 + c23 * (a * U1L + bb * V1L);
-                acc[0] += wl * u0;
-                acc[1] += wl * fsx * T1;
-                acc[2] += wl * fsy * T2;
-                acc[3] += wl * fsxy * T3;
+                if (use_corr) {
+                  // adjoint correlation (low-memory): cell averages of this sweep (the multiplier of the opposite
+                  // direction) times the stored forward psi0 of that direction
+                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
+                } else {
+                  acc[0] += wl * u0;
+                  acc[1] += wl * fsx * T1;
+                  acc[2] += wl * fsy * T2;
+                  acc[3] += wl * fsxy * T3;
+                }
                 if (VAR == 2) {
                   acc[NR - 2] += wl * fsx * rec1;
                   acc[NR - 1] += wl * fsy * rec2;
@@ -518,7 +611,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
     o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * s[1];
     o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * s[2];
     o3 = m * (1.0 / 9.0) * (0.0 - xb.y) - 0.5 * h * s[3];
-    if (source) { o1 += sq1[3 * (size_t)K]; o2 += sq1[3 * (size_t)K + 1]; o3 += sq1[3 * (size_t)K + 2]; }
+    if (source && sq1) { o1 += sq1[3 * (size_t)K]; o2 += sq1[3 * (size_t)K + 1]; o3 += sq1[3 * (size_t)K + 2]; }
   }
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K) = make_double2(o0, o1);
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(o2, o3);
@@ -569,15 +662,15 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
     switch (variant) {
       case LMDG_STD:
         prep_kernel<T, 0><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
-                                            qiso, src, sh);
+                                            qiso, src, sh, a.coef ? a.mat : nullptr);
         break;
       case LMDG_LM:
         prep_kernel<T, 1><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
-                                            qiso, src, sh);
+                                            qiso, src, sh, a.coef ? a.mat : nullptr);
         break;
       default:
         prep_kernel<T, 2><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
-                                            qiso, src, sh);
+                                            qiso, src, sh, a.coef ? a.mat : nullptr);
         break;
     }
   }

@@ -57,7 +57,7 @@ def build(force=False):
 def _lib():
     global _LIB
     if _LIB is None:
-        path = _build_mod.LIB
+        path = os.environ.get("LMDG_LIB") or _build_mod.LIB
         if not os.path.exists(path):
             raise ImportError(f"liblmdg is not built ({path}); run paper_1907_01027_gb300.build.build()")
         L = ctypes.CDLL(path)

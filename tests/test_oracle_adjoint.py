@@ -57,3 +57,22 @@ def test_dense_adjoint_finite_differences():
         pq = copy.deepcopy(p)
         pq.q[K, 0] += 1.0
         assert abs((_J(pq, g) - J) - dq[K]) <= 1e-12 * max(abs(dq[K]), abs(J))
+
+
+def test_lowmem_dense_adjoint_finite_differences():
+    p = random_problem(3, 4, 1.0, 6, q_per_angle=False)
+    g = np.random.default_rng(3).uniform(0, 1, p.nx)
+    J, dss, dsa, dq = dense.adjoint(p, g, "lm")
+    for K in (0, 5):
+        for field, ref in (("sigma_s", dss), ("sigma_a", dsa)):
+            d = 1e-4 * getattr(p, field)[K]
+            pp, pm = copy.deepcopy(p), copy.deepcopy(p)
+            getattr(pp, field)[K] += d
+            getattr(pm, field)[K] -= d
+            fd = (_Jlm(pp, g) - _Jlm(pm, g)) / (2 * d)
+            assert abs(fd - ref[K]) <= 1e-6 * abs(ref[K]), (field, K, fd, ref[K])
+
+
+def _Jlm(p, g):
+    phi = dense.solve(p, "lm")["phi"]
+    return float(np.sum(g * p.h * p.h * phi[:, 0]))
