@@ -101,6 +101,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(total_ms, updates, dist):
+    """Whole-job figures over the ranks: the timed region is the slowest rank's, the work is every rank's
+    (weak scaling: each rank runs the full workload as an independent replica; no data-path collective)."""
+    if dist is None:
+        return total_ms, updates
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -207,13 +221,7 @@ def run_gpu(args, rank, ws, dist):
     total_ms = sum(durations)
     sweeps = sum(st["sweeps_fp32"] + st["sweeps_fp64"] for _, st in stats)
     updates = sweeps * upd
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        updates = float(u.item())
+    total_ms, updates = aggregate(total_ms, updates, dist)
     value = updates / (total_ms / 1e3)
     launches = sum(st["launches"] for _, st in stats)
 
