@@ -1,0 +1,67 @@
+"""Argument validation of lmdg_setup (host logic, runs before any device work, so it is checked on the CPU)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads.problems import uniform_problem
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1907_01027_gb300 import lmdg
+    try:
+        return lmdg._lib()
+    except ImportError:
+        pytest.skip("liblmdg not built")
+
+
+def _setup(L, p, eps=None, variant=0, ox=None, oy=None, w=None, nang=None):
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad
+    ox = np.ascontiguousarray(p.ox if ox is None else ox)
+    oy = np.ascontiguousarray(p.oy if oy is None else oy)
+    w = np.ascontiguousarray(p.w if w is None else w)
+    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    quad = Quad(len(w) if nang is None else nang, ox.ctypes.data, oy.ctypes.data, w.ctypes.data)
+    ss = np.ascontiguousarray(p.sigma_s)
+    sa = np.ascontiguousarray(p.sigma_a)
+    q = np.ascontiguousarray(p.q)
+    h = ctypes.c_void_p()
+    rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ss.ctypes.data, sa.ctypes.data,
+                      q.ctypes.data, 1, None, float(p.eps if eps is None else eps), variant, None)
+    if rc == 0:
+        L.lmdg_destroy(h)
+    return rc
+
+
+def test_invalid_arguments_rejected(L):
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    assert _setup(L, p, eps=0.0) == -1
+    assert _setup(L, p, eps=-1.0) == -1
+    assert _setup(L, p, variant=3) == -1
+    bad = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    bad.sigma_a[3] = -0.1
+    assert _setup(L, bad) == -1
+    zero = uniform_problem(4, 4, 0.0, 0.0, 1.0)             # sigma_t = 0
+    assert _setup(L, zero) == -1
+
+
+def test_invalid_quadrature_rejected(L):
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    ox = p.ox.copy()
+    ox[0] = 0.0                                                # a direction on an axis
+    assert _setup(L, p, ox=ox) == -2
+    w = p.w * 1.01                                             # weights not summing to 1
+    assert _setup(L, p, w=w) == -2
+    assert _setup(L, p, nang=len(p.w) - 1) == -2               # not a multiple of 4
+    oy = p.oy.copy()
+    oy[0] = -oy[0]                                             # unequal quadrant populations
+    assert _setup(L, p, oy=oy) == -2
+
+
+def test_valid_arguments_reach_the_device(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("valid setup is exercised by the GPU tests")
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    assert _setup(L, p) == -4                                  # validated, then no CUDA device here
