@@ -198,25 +198,30 @@ void osw_sweep_L00(int n, double h, double ox, double oy, const double *sigt, co
 
 /* Upwind reconstruction of one angle at cell (i, j) from cell averages u0 with alpha = 0
  * (R Pi_0, Section 3.3.1): Legendre coefficients of the P1 slopes, (h/2) delta_x on b1 and (h/2) delta_y on
- * b2, using the upwind difference (s_x = -sign(Omega_x)) and spacing h/2 against the zero boundary value. */
-static void recon0(int n, double h, double ox, double oy, const double *u0, int i, int j, double sl[2]) {
+ * b2, using the upwind difference (s_x = -sign(Omega_x)) and spacing h/2 against the zero boundary value.
+ * supp (may be NULL): per-cell face bits (1 west, 2 east, 4 south, 8 north) of interior faces across which
+ * the reconstruction is suppressed (Section 4, the discontinuous cross-section examples): the difference
+ * across such a face is taken as zero. */
+static void recon0(int n, double h, double ox, double oy, const double *u0, const unsigned char *supp, int i,
+                   int j, double sl[2]) {
   int K = j * n + i;
+  unsigned m = supp ? supp[K] : 0u;
   double dx, dy;
-  if (ox > 0) dx = i > 0 ? (u0[K] - u0[K - 1]) / h : (u0[K] - 0.0) / (h / 2);
-  else dx = i < n - 1 ? (u0[K + 1] - u0[K]) / h : (0.0 - u0[K]) / (h / 2);
-  if (oy > 0) dy = j > 0 ? (u0[K] - u0[K - n]) / h : (u0[K] - 0.0) / (h / 2);
-  else dy = j < n - 1 ? (u0[K + n] - u0[K]) / h : (0.0 - u0[K]) / (h / 2);
+  if (ox > 0) dx = i > 0 ? ((m & 1u) ? 0.0 : (u0[K] - u0[K - 1]) / h) : (u0[K] - 0.0) / (h / 2);
+  else dx = i < n - 1 ? ((m & 2u) ? 0.0 : (u0[K + 1] - u0[K]) / h) : (0.0 - u0[K]) / (h / 2);
+  if (oy > 0) dy = j > 0 ? ((m & 4u) ? 0.0 : (u0[K] - u0[K - n]) / h) : (u0[K] - 0.0) / (h / 2);
+  else dy = j < n - 1 ? ((m & 8u) ? 0.0 : (u0[K + n] - u0[K]) / h) : (0.0 - u0[K]) / (h / 2);
   sl[0] = 0.5 * h * dx;
   sl[1] = 0.5 * h * dy;
 }
 
 /* row 0 of L_l applied to the trial function u0 b0 + R u0 at cell (i, j), given u0 on K and upwind cells */
 static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, double sigt, const double *u0,
-                       int i, int j) {
+                       const unsigned char *supp, int i, int j) {
   int K = j * n + i;
   double A[4][4], uK[4], sl[2];
   diag_block(e, ox, oy, sigt, A);
-  recon0(n, h, ox, oy, u0, i, j, sl);
+  recon0(n, h, ox, oy, u0, supp, i, j, sl);
   uK[0] = u0[K]; uK[1] = sl[0]; uK[2] = sl[1]; uK[3] = 0.0;
   double s = 0.0;
   for (int q = 0; q < 4; ++q) s += A[0][q] * uK[q];
@@ -226,7 +231,7 @@ static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, d
     if (on < 0 && k >= 0) {
       int ki = k % n, kj = k / n;
       double uk[4], sk[2];
-      recon0(n, h, ox, oy, u0, ki, kj, sk);
+      recon0(n, h, ox, oy, u0, supp, ki, kj, sk);
       uk[0] = u0[k]; uk[1] = sk[0]; uk[2] = sk[1]; uk[3] = 0.0;
       for (int q = 0; q < 4; ++q) s += on * e->nbrf[f][0][q] * uk[q];
     }
@@ -237,8 +242,9 @@ static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, d
 /* Solve Ltilde00 u0 = b0 for one angle, Ltilde00 = L00 + L01 R (Section 3.3.2): row 0 of L applied to the
  * reconstructed trial function.  The reconstruction at K uses only K and its upwind neighbours, so the
  * system is lower triangular in sweep order; each cell's equation is affine in u0[K] and is solved from two
- * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [n*n]. */
-void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, const double *b0, double *u0) {
+ * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [n*n]; supp: suppression bits as in recon0, or NULL. */
+void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, const double *b0, double *u0,
+                    const unsigned char *supp) {
   elem_t e;
   build_elem(h, &e);
   memset(u0, 0, sizeof(double) * (size_t)n * n);
@@ -248,9 +254,9 @@ void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, c
       int i = ox > 0 ? ii : n - 1 - ii;
       int K = j * n + i;
       u0[K] = 0.0;
-      double r0 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, i, j);
+      double r0 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, i, j);
       u0[K] = 1.0;
-      double r1 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, i, j);
+      double r1 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, i, j);
       u0[K] = (b0[K] - r0) / (r1 - r0);
     }
   }

@@ -141,17 +141,30 @@ def assemble(p):
     return L, S, Q
 
 
-def reconstruct(p, u0, alpha):
+def _same_material(p):
+    """(sx, sy): sx[j, f] is True when cells (f, j) and (f + 1, j) have equal (sigma_s, sigma_a), sy[f, i]
+    likewise for cells (i, f) and (i, f + 1)."""
+    n = p.n
+    ss, sa = p.sigma_s.reshape(n, n), p.sigma_a.reshape(n, n)
+    sx = (ss[:, 1:] == ss[:, :-1]) & (sa[:, 1:] == sa[:, :-1])
+    sy = (ss[1:, :] == ss[:-1, :]) & (sa[1:, :] == sa[:-1, :])
+    return sx, sy
+
+
+def reconstruct(p, u0, alpha, suppress=False):
     """Upwind reconstruction R_alpha Pi_0 (Section 3.3.1), 2D P1 slopes only.
 
     ``u0``: cell averages ``[n_Omega][n_x]``.  Returns the Legendre coefficients ``[n_Omega][n_x][4]`` of
     (delta_x u)(x - x_i) + (delta_y u)(y - y_j): coefficient of b1 = xi is (h/2) delta_x, of b2 = eta is
     (h/2) delta_y.  delta uses the upwind side s_x = -sign(Omega_x); at the inflow boundary the difference is
     taken with alpha at the face midpoint over a spacing h/2 (alpha None means 0).  The face-midpoint value
-    of the linear face data (a0 + a1 t) is a0.
+    of the linear face data (a0 + a1 t) is a0.  ``suppress``: no reconstruction across an interior face where
+    the cross sections jump (the remedy Section 4 applies to the kinks at a discontinuity): the upwind
+    difference across such a face is zero.
     """
     n, h, na = p.n, p.h, p.nang
     out = np.zeros((na, n * n, 4))
+    same_x, same_y = _same_material(p) if suppress else (None, None)
     for l in range(na):
         U = u0[l].reshape(n, n)              # [j][i]
         dx = np.zeros((n, n))
@@ -172,14 +185,23 @@ def reconstruct(p, u0, alpha):
             dy[:-1, :] = (U[1:, :] - U[:-1, :]) / h
             aN = alpha[l, 3, :, 0] if alpha is not None else np.zeros(n)
             dy[-1, :] = (aN - U[-1, :]) / (h / 2)
+        if suppress:
+            if p.ox[l] > 0:
+                dx[:, 1:] *= same_x
+            else:
+                dx[:, :-1] *= same_x
+            if p.oy[l] > 0:
+                dy[1:, :] *= same_y
+            else:
+                dy[:-1, :] *= same_y
         out[l, :, 1] = (h / 2) * dx.ravel()
         out[l, :, 2] = (h / 2) * dy.ravel()
     return out
 
 
-def _Rstar(p, u0, alpha):
+def _Rstar(p, u0, alpha, suppress=False):
     """R*_alpha applied to the piecewise constants u0: R_alpha Pi_0 u minus its angular average."""
-    R = reconstruct(p, u0, alpha)
+    R = reconstruct(p, u0, alpha, suppress)
     return R - np.einsum("l,lkr->kr", p.w, R)[None]
 
 
@@ -199,7 +221,7 @@ def lm_basis(p):
     return E
 
 
-def rlm_trial_basis(p):
+def rlm_trial_basis(p, suppress=False):
     """Trial basis of V_h^rlm: xi^{l,p,0} + R*_0 xi^{l,p,0}, then eta^{p,r} (Section 3.3.2)."""
     na, nx = p.nang, p.nx
     E = lm_basis(p)
@@ -208,13 +230,14 @@ def rlm_trial_basis(p):
         for K in range(nx):
             u0 = np.zeros((na, nx))
             u0[l, K] = 1.0
-            Rs = _Rstar(p, u0, None)
+            Rs = _Rstar(p, u0, None, suppress)
             Et[:, l * nx + K] += Rs.ravel()
     return Et
 
 
-def solve(p, variant):
-    """Solve the discrete problem.  Returns a dict with
+def solve(p, variant, suppress=False):
+    """Solve the discrete problem (``suppress``: RLMDG without reconstruction across cross-section jumps).
+    Returns a dict with
 
     ``psi``  full coefficients [n_Omega][n_x][4] of the (reconstructed) discrete solution,
     ``phi``  scalar flux moments sum_l w_l psi_l, [n_x][4],
@@ -235,8 +258,8 @@ def solve(p, variant):
         out["phi1"] = c[na * nx:].reshape(nx, 3)
     elif variant == "rlm":
         E = lm_basis(p)
-        Et = rlm_trial_basis(p)
-        rho = _Rstar(p, np.zeros((na, nx)), p.alpha).ravel()   # affine part R*_alpha 0
+        Et = rlm_trial_basis(p, suppress)
+        rho = _Rstar(p, np.zeros((na, nx)), p.alpha, suppress).ravel()   # affine part R*_alpha 0
         c = np.linalg.solve(E.T @ B @ Et, E.T @ (Q - B @ rho))
         psi = (Et @ c + rho).reshape(na, nx, 4)
         out["psi0"] = c[:na * nx].reshape(na, nx)

@@ -38,10 +38,13 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(_build.build())
         dp = ctypes.POINTER(ctypes.c_double)
-        for name in ("osw_apply_L", "osw_sweep_L", "osw_sweep_L00", "osw_sweep_Lt00", "osw_apply_LT", "osw_sweep_LT"):
+        for name in ("osw_apply_L", "osw_sweep_L", "osw_sweep_L00", "osw_apply_LT", "osw_sweep_LT"):
             f = getattr(lib, name)
             f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
             f.restype = None
+        lib.osw_sweep_Lt00.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                       ctypes.POINTER(ctypes.c_ubyte)]
+        lib.osw_sweep_Lt00.restype = None
         lib.osw_elem_tables.argtypes = [ctypes.c_double, dp]
         lib.osw_elem_tables.restype = None
         _lib = lib
@@ -63,10 +66,12 @@ class SweepOracle:
     """Matrix-free block operators of one problem.  ``threads`` angles are processed concurrently; every
     angular sum is accumulated in angle order, so results do not depend on the thread count."""
 
-    def __init__(self, p, threads=None, literal_b11=False):
+    def __init__(self, p, threads=None, literal_b11=False, suppress=False):
         self.p = p
         self.literal_b11 = literal_b11
         self.n, self.h, self.nx, self.na = p.n, p.h, p.nx, p.nang
+        self.suppress = suppress
+        self.supp = self._suppression_bits() if suppress else None
         self.sigt = np.ascontiguousarray(p.sigma_s / p.eps + p.eps * p.sigma_a, dtype=np.float64)
         self.sse = p.sigma_s / p.eps
         self.mass = elem_tables(p.h)["mass"]
@@ -74,12 +79,28 @@ class SweepOracle:
         self.lib = _load()
         self.cg_iters = 0
 
+    def _suppression_bits(self):
+        """Interior faces where (sigma_s, sigma_a) jumps: per cell, bit 1 west, 2 east, 4 south, 8 north.  With
+        ``suppress`` the RLMDG reconstruction takes no difference across these faces (the remedy for the kinks
+        at cross-section discontinuities, Section 4)."""
+        n, p = self.n, self.p
+        ss, sa = p.sigma_s.reshape(n, n), p.sigma_a.reshape(n, n)
+        bits = np.zeros((n, n), dtype=np.uint8)
+        for j in range(n):
+            for i in range(n):
+                for bit, (jj, ii) in ((1, (j, i - 1)), (2, (j, i + 1)), (4, (j - 1, i)), (8, (j + 1, i))):
+                    if 0 <= ii < n and 0 <= jj < n and (ss[j, i] != ss[jj, ii] or sa[j, i] != sa[jj, ii]):
+                        bits[j, i] |= bit
+        return bits.ravel()
+
     # ---------------------------------------------------------------- per-angle primitives (Lhat_l)
     def _call(self, name, l, a, size):
         out = np.zeros(size)
         a = np.ascontiguousarray(a, dtype=np.float64)
-        getattr(self.lib, name)(self.n, self.h, float(self.p.ox[l]), float(self.p.oy[l]), _ptr(self.sigt),
-                                _ptr(a), _ptr(out))
+        args = [self.n, self.h, float(self.p.ox[l]), float(self.p.oy[l]), _ptr(self.sigt), _ptr(a), _ptr(out)]
+        if name == "osw_sweep_Lt00":
+            args.append(None if self.supp is None else self.supp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        getattr(self.lib, name)(*args)
         return out
 
     def L(self, l, u):
@@ -282,6 +303,10 @@ class SweepOracle:
             up = np.concatenate([U[1:, :], bn[None, :]], axis=0)
             sp = np.concatenate([np.full((n - 1, n), h), np.full((1, n), h / 2)], axis=0)
             dy = (up - U) / sp
+        if self.supp is not None:
+            m = self.supp.reshape(n, n)
+            dx = np.where(m & (1 if p.ox[l] > 0 else 2), 0.0, dx)
+            dy = np.where(m & (4 if p.oy[l] > 0 else 8), 0.0, dy)
         return np.stack([0.5 * h * dx.ravel(), 0.5 * h * dy.ravel()], axis=1)
 
     def r_alpha(self, l):

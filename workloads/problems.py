@@ -172,11 +172,13 @@ def mms_problem(n, N, psi, dpsi_dx, dpsi_dy, sigma_s=1.0, sigma_a=1.0, eps=1.0, 
                 npts=5, name="mms"):
     """Manufactured solution ``psi(x, y, ox, oy)``: builds the angle-dependent source from the continuous
     residual of eq-main (with the discrete angular average, as in eq:sn) and ``alpha = psi`` on the
-    boundary.  ``info['phi_avg']`` holds the exact cell averages of the scalar flux."""
+    boundary.  ``info['phi_avg']`` holds the exact cell averages of the scalar flux.  ``sigma_s`` and
+    ``sigma_a`` are numbers or functions of (x, y) constant on every cell (a layered or patched medium)."""
     ox, oy, w = level_symmetric_2d(N)
     h = L / n
     nang = len(w)
-    sig_t = sigma_s / eps + eps * sigma_a
+    ss = sigma_s if callable(sigma_s) else (lambda x, y, v=float(sigma_s): v + 0 * x)
+    sa = sigma_a if callable(sigma_a) else (lambda x, y, v=float(sigma_a): v + 0 * x)
 
     def psibar(x, y):
         return sum(w[m] * psi(x, y, ox[m], oy[m]) for m in range(nang))
@@ -187,14 +189,18 @@ def mms_problem(n, N, psi, dpsi_dx, dpsi_dy, sigma_s=1.0, sigma_a=1.0, eps=1.0, 
         a, b = ox[l], oy[l]
 
         def ql(x, y, a=a, b=b):
+            sig_t = ss(x, y) / eps + eps * sa(x, y)
             return (a * dpsi_dx(x, y, a, b) + b * dpsi_dy(x, y, a, b) + sig_t * psi(x, y, a, b)
-                    - (sigma_s / eps) * psibar(x, y)) / eps
+                    - (ss(x, y) / eps) * psibar(x, y)) / eps
         q[l] = legendre_project_cell(ql, n, h, x0, y0, npts)
         alpha[l] = legendre_project_face(lambda x, y, a=a, b=b: psi(x, y, a, b), n, h, x0, y0, npts)
     phi = legendre_project_cell(psibar, n, h, x0, y0, npts)[:, 0]
-    nx = n * n
-    return Problem(n=n, h=h, x0=x0, y0=y0, ox=ox, oy=oy, w=w, sigma_s=np.full(nx, float(sigma_s)),
-                   sigma_a=np.full(nx, float(sigma_a)), q=q, eps=eps, alpha=alpha, name=name,
+    xc = x0 + (np.arange(n) + 0.5) * h
+    yc = y0 + (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, yc)                     # [j][i]
+    return Problem(n=n, h=h, x0=x0, y0=y0, ox=ox, oy=oy, w=w,
+                   sigma_s=np.asarray(ss(X, Y), dtype=float).ravel(),
+                   sigma_a=np.asarray(sa(X, Y), dtype=float).ravel(), q=q, eps=eps, alpha=alpha, name=name,
                    info={"phi_avg": phi})
 
 
