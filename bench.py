@@ -29,7 +29,7 @@ VARIANTS = ("std", "lm", "rlm")
 
 # FP32 operations per cell-angle update in the sweep kernel (counted from the kernel source, FMA = 2;
 # reciprocals count 1): standard Q1 block solve, low-memory row-0 solve + L-row reductions, reconstructed.
-FLOPS_PER_UPDATE = {"std": 104, "lm": 56, "rlm": 70}
+FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 
 
 def workload_config():
@@ -330,24 +330,25 @@ def run_gpu(args, rank, ws, dist):
 
 
 def run_profile(args):
-    """Small case for ncu: 512x512 cells, S16, the bench media; one FP32 LMDG sweep (non-storing), one FP32
-    Q1-DG storing sweep (psi 604 MB, larger than L2) and one FP64 LMDG sweep, after one untimed sweep of each."""
+    """Small case for ncu: 512x512 cells, S16, the bench media; per round an FP32 LMDG sweep (non-storing), an
+    FP32 Q1-DG storing sweep (psi 604 MB, larger than L2) and FP64 Q1-DG, LMDG and RLMDG sweeps (as in the
+    refinement residual); two rounds (sweep kernels 1-5 untimed, 6-10 for the capture)."""
     import torch
     from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
     from workloads.problems import config4
     torch.cuda.set_device(0)
     p = config4(eps=1.0, n=512)
-    lm = Context(p, "lm", precision=FP32)
-    st = Context(p, "std", precision=FP32)
+    ctx = {v: Context(p, v, precision=FP32) for v in ("std", "lm", "rlm")}
     x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(2):
-        lm.sweep(x, y, flags=SWEEP_FP32)
-        st.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
-        lm.sweep(x, y, flags=0)
+        ctx["lm"].sweep(x, y, flags=SWEEP_FP32)
+        ctx["std"].sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+        for v in ("std", "lm", "rlm"):
+            ctx[v].sweep(x, y, flags=SWEEP_SOURCE)
         torch.cuda.synchronize()
-    lm.close()
-    st.close()
+    for c in ctx.values():
+        c.close()
     print("profile case done", flush=True)
     return 0
 

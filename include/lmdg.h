@@ -87,6 +87,9 @@ typedef struct {
   int precond;         /* 1 (default): right preconditioner diag(I, diag(B11))^-1 for LMDG/RLMDG; 0: none */
   long long spin_limit;/* polls of a readiness flag before a sweep reports LMDG_ERR_TIMEOUT (default 2^26) */
   int device;          /* CUDA device ordinal (default 0) */
+  int suppress;        /* LMDG_RLM only, 1: no reconstruction across an interior face where sigma_s or sigma_a
+                          changes (the remedy of Section 4 for the kinks at a cross-section discontinuity: the
+                          upwind difference across such a face is zero); default 0 */
 } lmdg_options;
 
 typedef struct {

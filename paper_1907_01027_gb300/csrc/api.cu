@@ -80,6 +80,7 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     a.p1ra = nullptr;
   }
   if constexpr (sizeof(T) == 8) a.corr = c->corr;
+  a.supp = c->supp;
   a.coef = nullptr; a.ncoef = 0; a.ncls = 0; a.cls = nullptr; a.matsh = nullptr; a.mat = nullptr;
   if constexpr (sizeof(T) == 8) {
     if (c->coef) {
@@ -123,7 +124,7 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   CK(cudaEventRecord(c->ev1, s));
   c->ev_pending = f64 ? 0 : 1;
   // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
-  CK(launch_epilogue<T>(c->variant, c->n, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse,
+  CK(launch_epilogue<T>(c->variant, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
                         c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
   if (f64) c->sweeps64++; else c->sweeps32++;
   return 0;
@@ -284,6 +285,7 @@ int lmdg_default_options(lmdg_options *o) {
   o->precond = 1;
   o->spin_limit = 1LL << 26;
   o->device = 0;
+  o->suppress = 0;
   return 0;
 }
 
@@ -319,10 +321,10 @@ void lmdg_destroy(lmdg_ctx *c) {
   free_pd(c->d64);
   free_pd(c->d32);
   cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11diag);
-  cudaFree(c->sigma_a); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
+  cudaFree(c->sigma_a); cudaFree(c->qmom); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
   cudaFree(c->cellsrc); cudaFree(c->cellsh);
   cudaFree(c->rev); cudaFree(c->qadj64); cudaFree(c->qadj32); cudaFree(c->adj_buf);
-  cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh); cudaFree(c->coef);
+  cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh); cudaFree(c->coef); cudaFree(c->supp);
   cudaFree(c->V);
   for (auto &v : c->vec) cudaFree(v);
   cudaFree(c->red);
@@ -365,7 +367,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   lmdg_options o;
   lmdg_default_options(&o);
   if (opt) o = *opt;
-  if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1)
+  if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
+      (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM))
     return LMDG_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
@@ -449,6 +452,12 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     }
   }
   c->Ax[0] = Ax[0]; c->Ax[1] = Ax[1]; c->Ay[0] = Ay[0]; c->Ay[1] = Ay[1];
+  // quadrature moments of the epilogue: sum w, sum w |Omega_x|, sum w |Omega_y|, sum w Omega_x, sum w Omega_y
+  std::vector<double> qm(5, 0.0);
+  for (int l = 0; l < na; ++l) {
+    qm[0] += w[l]; qm[1] += w[l] * std::fabs(ox[l]); qm[2] += w[l] * std::fabs(oy[l]);
+    qm[3] += w[l] * ox[l]; qm[4] += w[l] * oy[l];
+  }
   // diagonal of B11: eps sigma_a h^2 D_r + outflow face terms (Jacobi right preconditioner)
   std::vector<double> bd(nx * 3);
   const double fx[3] = {1.0, 1.0 / 3.0, 1.0 / 3.0}, fy[3] = {1.0 / 3.0, 1.0, 1.0 / 3.0};
@@ -480,10 +489,27 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
       (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qv)) ||
       (e = upload(&c->p1ra64, p1ra)) || (e = upload(&c->p1ra32, p1ra)) || (e = upload(&c->sq1, sq1)) ||
-      (e = upload(&c->b11diag, bd)) || (e = upload(&c->sigma_a, sa)))
+      (e = upload(&c->b11diag, bd)) || (e = upload(&c->sigma_a, sa)) || (e = upload(&c->qmom, qm)))
     return fail(e);
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
+  }
+  if (o.suppress) {
+    // interior faces across which (sigma_s, sigma_a) changes: no RLMDG reconstruction there
+    std::vector<double> bits(nx, 0.0);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const size_t K = (size_t)j * n + i;
+        unsigned m = 0;
+        const int ni[4] = {i - 1, i + 1, i, i}, nj[4] = {j, j, j - 1, j + 1};
+        for (int f = 0; f < 4; ++f) {
+          if (ni[f] < 0 || ni[f] >= n || nj[f] < 0 || nj[f] >= n) continue;
+          const size_t Kn = (size_t)nj[f] * n + ni[f];
+          if (sigma_s[Kn] != sigma_s[K] || sigma_a[Kn] != sigma_a[K]) m |= 1u << f;
+        }
+        bits[K] = m;
+      }
+    if ((e = upload(&c->supp, bits))) return fail(e);
   }
   c->g64 = choose_geom(variant, n, c->nq, true);
   c->g32 = choose_geom(variant, n, c->nq, false);

@@ -17,13 +17,18 @@ SweepGeom env_override(SweepGeom best, int nq, int n) {
 }
 
 // One CTA per (quadrant, group, strip), W warps of APW directions, with the fewest groups for that shape (one
-// partial reduction array per quadrant-group).  Measured on the GB300 at 1024^2 cells, S16: the latency-bound
-// FP32 sweeps run fastest with one direction per warp and 8 warps per CTA (the most independent
-// cell-direction chains), even though not every CTA is then resident (the ticket order keeps the wavefront
-// deadlock-free); the FP64 sweeps, bound by the FP64 pipe, with two directions per warp and up to 6 warps.
+// partial reduction array per quadrant-group).  Measured on the GB300 at 1024^2 cells, S16 (sweep times in
+// ms of the chosen shape against the runner-up):
+//   FP32: one direction per warp, 8 warps for Q1-DG and RLMDG (2.42, 2.69; the latency-bound sweeps want
+//         the most independent cell-direction chains, even though not every CTA is then resident -- the
+//         ticket order keeps the wavefront deadlock-free); LMDG, whose per-direction work is smallest, two
+//         directions per warp and 6 warps (2.08 against 2.15);
+//   FP64 (FP64-pipe bound): Q1-DG one direction per warp, 4 warps (15.2 against 16.8 with two directions and
+//         6 warps); LMDG and RLMDG two directions per warp, 3 warps (9.2, 17.5).
 SweepGeom choose_geom(int variant, int n, int nq, bool fp64) {
-  (void)variant;
-  const int apw = fp64 ? 2 : 1, wmax = fp64 ? 6 : 8;
+  int apw, wmax;
+  if (fp64) { apw = variant == LMDG_STD ? 1 : 2; wmax = variant == LMDG_STD ? 4 : 3; }
+  else { apw = variant == LMDG_LM ? 2 : 1; wmax = variant == LMDG_LM ? 6 : 8; }
   int G = (nq + apw * wmax - 1) / (apw * wmax);
   while (G > 1 && (G - 1) * ((nq + G - 1) / G) >= nq) --G;
   const int gsize = (nq + G - 1) / G;

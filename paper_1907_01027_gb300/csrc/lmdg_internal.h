@@ -65,6 +65,7 @@ struct SweepArgs {
   const int *cls;      // [nang] sorted index -> direction class
   const double *matsh; // [materials] sigma_t h of each material
   const int *mat;      // [nx] material of each cell (prep_kernel writes it into the cellsh slot)
+  const unsigned *supp;  // RLMDG: [nx] faces without reconstruction (1 west, 2 east, 4 south, 8 north) or null
 };
 
 // Number of kernels launched by this library (all host wrappers add to it).
@@ -86,11 +87,14 @@ int sweep_blocks_per_sm(int variant, int warps, int apw);
 // launch shape for a problem (all CTAs resident when possible); LMDG_SWEEP_GEOM="groups,warps,apw" overrides
 SweepGeom choose_geom(int variant, int n, int nq, bool fp64);
 
-// y = K x - source * b  from the partial reductions (sweep.cu)
+// y = K x - source * b  from the partial reductions (sweep.cu); sigt = sigma_t per cell, qm = the quadrature
+// moments written by quad_moments
 template <typename T>
-cudaError_t launch_epilogue(int variant, int n, int nx, int P, double h, const T *part, const double *X,
-                            const double *sse, const double *p1ra, const double *sq1, int source,
-                            double *y, cudaStream_t s);
+cudaError_t launch_epilogue(int variant, int nx, int P, double h, const T *part, const double *X,
+                            const double *sse, const double *sigt, const double *qm, const double *p1ra,
+                            const double *sq1, int source, double *y, cudaStream_t s);
+// qm[0..4] = sum w, sum w |Omega_x|, sum w |Omega_y|, sum w Omega_x, sum w Omega_y over all directions
+cudaError_t quad_moments(int nang, const double *ox, const double *oy, const double *w, double *qm, cudaStream_t s);
 
 }  // namespace lmdg
 
@@ -109,6 +113,7 @@ struct lmdg_ctx {
   double *b11diag = nullptr;               // [nx][3] diagonal of B11 (Jacobi preconditioner)
   double *sigma_a = nullptr;               // [nx] (B11 stencil)
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};   // sum of w |Omega_x| over Omega_x > 0 / < 0, likewise y
+  double *qmom = nullptr;                  // device [5] quadrature moments (epilogue)
   lmdg::SweepGeom g64{}, g32{};
   void *part = nullptr;                    // partial reductions (double-sized)
   void *ytr = nullptr;                     // inter-strip traces (double-sized)
@@ -148,4 +153,5 @@ struct lmdg_ctx {
   int *cls = nullptr;                      // [nang] sorted index -> direction class
   double *matsh = nullptr;                 // [nmat] sigma_t h
   double *coef = nullptr;                  // [nmat][ncls][ncoef]
+  unsigned *supp = nullptr;                // RLMDG suppression bits per cell, or null
 };

@@ -88,8 +88,10 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   const SweepGeom g = geom_for(n, nq);
   const size_t nx = (size_t)n * n;
   const int NR = variant == LMDG_RLM ? 6 : 4;
-  // scratch layout: [perm (kMaxDirections ints)] [control words] [cell inputs] [partials] [strip traces]
-  const size_t off_ctrl = align256(sizeof(int) * kMaxDirections);
+  // scratch layout: [perm (kMaxDirections ints)] [quadrature moments] [control words] [cell inputs] [partials]
+  // [strip traces]
+  const size_t off_qm = align256(sizeof(int) * kMaxDirections);
+  const size_t off_ctrl = off_qm + align256(sizeof(double) * 5);
   const size_t off_cell = off_ctrl + align256(sizeof(unsigned) * (2 + (size_t)g.units()));
   const size_t off_cellh = off_cell + align256(sizeof(double) * 4 * nx);
   const size_t off_part = off_cellh + align256(sizeof(double) * nx);
@@ -125,9 +127,11 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   if (fill_u32(reinterpret_cast<unsigned *>(base + off_ytr), kTraceEmpty,
                2 * (size_t)n_omega * g.strips * n * 3, s) != cudaSuccess)
     return LMDG_ERR_CUDA;
+  double *qm = reinterpret_cast<double *>(base + off_qm);
+  if (quad_moments(n_omega, ox, oy, w, qm, s) != cudaSuccess) return LMDG_ERR_CUDA;
   if (launch_sweep<double>(variant, a, s) != cudaSuccess) return LMDG_ERR_CUDA;
-  if (launch_epilogue<double>(variant, n, (int)nx, 4 * g.groups, h, a.part, x, sigma_s_over_eps, nullptr, nullptr,
-                              0, y, s) != cudaSuccess)
+  if (launch_epilogue<double>(variant, (int)nx, 4 * g.groups, h, a.part, x, sigma_s_over_eps, sigma_t, qm, nullptr,
+                              nullptr, 0, y, s) != cudaSuccess)
     return LMDG_ERR_CUDA;
   unsigned err = 0;
   if (cudaMemcpyAsync(&err, a.ctrl + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

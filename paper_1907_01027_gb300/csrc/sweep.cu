@@ -31,9 +31,14 @@
 //
 // Reductions per cell (summed over the group's directions in a fixed order, one partial per quadrant-group):
 //   LMDG_STD : P psi = sum w psi                                  (4 moments)
-//   LMDG_LM  : P0 psi0 and sum_l w_l L_l(u_l; b_r), r = 1..3      (u_l the full per-direction trial function)
+//   LMDG_LM  : P0 psi0 and the direction-dependent part of sum_l w_l L_l(u_l; b_r), r = 1..3 (u_l the full
+//              per-direction trial function)
 //   LMDG_RLM : as LM, plus P1 R psi0 (2 slope moments)
-// from which the epilogue forms the reduced operator (see epilogue_kernel).
+// from which the epilogue forms the reduced operator (see epilogue_kernel).  In the low-memory schemes the
+// slopes of u_l are the isotropic X_1..3 (plus the reconstruction): their terms in L_l(u_l; b_r) that involve
+// only the cell itself are a quadrature moment times the cell's slopes, added once per cell by the epilogue;
+// the terms through the slope traces of the upwind cells (the same for every direction of LMDG) are summed
+// once per lane and warp.  What remains per direction is the row-0 solve and the face terms of u0.
 #include "lmdg_internal.h"
 
 namespace lmdg {
@@ -115,15 +120,28 @@ __device__ __forceinline__ double ld_relaxed_t(const double *p) {
   return v;
 }
 
+// Sign flip by the bit pattern (an integer op instead of an FP64 multiply): m = 0 keeps v, m = 0x80000000 negates.
+__device__ __forceinline__ double flip(double v, unsigned m) {
+  return __hiloint2double(__double2hiint(v) ^ (int)m, __double2loint(v));
+}
+__device__ __forceinline__ float flip(float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); }
+
+// With coefficient tables the sigma_t h slot of the staged cell data carries the material index as a bit pattern.
+__device__ __forceinline__ double mat_bits(int m, double) { return __longlong_as_double((long long)m); }
+__device__ __forceinline__ float mat_bits(int m, float) { return __int_as_float(m); }
+__device__ __forceinline__ int mat_of(double v) { return (int)__double_as_longlong(v); }
+__device__ __forceinline__ int mat_of(float v) { return __float_as_int(v); }
+
 }  // namespace
 
 // Shared-memory bytes of one CTA: partial reductions [2][kChunk][W][NR][32], cell data [2][kChunk][32][4] and
-// [2][kChunk][32], upstream traces [W][APW][kChunk][NS].
+// [2][kChunk][32], upstream traces [W][APW][kChunk][NS], RLMDG suppression bits [2][kChunk][32].
 template <typename T>
 size_t sweep_smem_bytes(int variant, int warps, int apw) {
   const int NR = variant == LMDG_RLM ? 6 : 4, NS = variant == LMDG_RLM ? 3 : 2;
   return sizeof(T) * ((size_t)2 * kChunk * warps * NR * 32 + (size_t)2 * kChunk * 32 * 5 +
-                      (size_t)warps * apw * kChunk * NS);
+                      (size_t)warps * apw * kChunk * NS) +
+         sizeof(unsigned) * (size_t)2 * kChunk * 32;
 }
 
 // Per-cell inputs of one sweep, global basis: src = 2h D_r (sigma_s/eps X_r + eps q_r) for the standard
@@ -160,15 +178,18 @@ __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, co
   }
   T *d = src + 4 * (size_t)K;
   d[0] = o[0]; d[1] = o[1]; d[2] = o[2]; d[3] = o[3];
-  sh[K] = mat ? (T)mat[K] : sigt[K] * h;
+  sh[K] = mat ? mat_bits(mat[K], (T)0) : sigt[K] * h;
 }
 
 // Coefficients of the element solves for one material (s = sigma_t h) and one direction class (a, b) =
-// (|Omega_x|, |Omega_y|), in the local frame of the kernel:
+// (|Omega_x|, |Omega_y|), in the local frame of the kernel, with d0 = 2(a + b + s), d1 = 2a + 2/3 (b + s),
+// d2 = 2b + 2/3 (a + s), d3 = 2/3 (a + b) + 2/9 s:
 //   standard: i1 = 1/d1, i2 = 1/d2, p1 = 2a i1, p2 = 2b i2, q1 = 2/3 b i1, q2 = 2/3 a i2, and with the 2x2 Schur
 //             system (a00 a03; a03 a33) of the (u0, u3) unknowns, c0 = a33/det, c1 = a03/det, c3 = a00/det;
-//   low-memory: 1/d0 (LMDG) or 1/(d0 + a + b) (RLMDG interior cells), d1, d2, d3.
-int coef_count(int variant) { return variant == LMDG_STD ? 9 : 4; }
+//   LMDG: 1/d0;
+//   RLMDG: 1/(d0 + cx + cy) with cx = a for a reconstructed x slope, 2a on an inflow x face, 0 where the
+//          reconstruction is suppressed (likewise cy), at index (x state) + 3 (y state), states in that order.
+int coef_count(int variant) { return variant == LMDG_STD ? 9 : (variant == LMDG_LM ? 1 : 9); }
 
 __global__ void coef_kernel(int variant, int nmat, int ncls, const double *__restrict__ matsh,
                             const double *__restrict__ cls_ab, double *__restrict__ coef) {
@@ -187,10 +208,13 @@ __global__ void coef_kernel(int variant, int nmat, int ncls, const double *__res
     const double det = a00 * a33 - a03 * a03;
     o[0] = i1; o[1] = i2; o[2] = 2 * a * i1; o[3] = 2 * b * i2; o[4] = c23 * b * i1; o[5] = c23 * a * i2;
     o[6] = a33 / det; o[7] = a03 / det; o[8] = a00 / det;
+  } else if (variant == LMDG_LM) {
+    coef[id] = 1.0 / d0;
   } else {
-    double *o = coef + (size_t)id * 4;
-    o[0] = variant == LMDG_LM ? 1.0 / d0 : 1.0 / (d0 + a + b);
-    o[1] = d1; o[2] = d2; o[3] = d3;
+    double *o = coef + (size_t)id * 9;
+    const double cx[3] = {a, 2 * a, 0.0}, cy[3] = {b, 2 * b, 0.0};
+    for (int ys = 0; ys < 3; ++ys)
+      for (int xs = 0; xs < 3; ++xs) o[xs + 3 * ys] = 1.0 / (d0 + cx[xs] + cy[ys]);
   }
 }
 
@@ -207,14 +231,16 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 #define LMDG_MINB32 2
 #endif
 
-template <typename T, int VAR, int APW>
+// TAB: the element-solve coefficients come from the FP64 tables (FP64 instances only), else they are formed in
+// the kernel from sigma_t h.
+template <typename T, int VAR, int APW, bool TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr int NR = (VAR == 2) ? 6 : 4;   // reduced values per cell
   constexpr int NS = (VAR == 2) ? 3 : 2;   // trace values passed downwind per face
+  constexpr int NC = VAR == 0 ? 9 : (VAR == 1 ? 1 : 9);   // table coefficients per (material, class)
   constexpr int C = kChunk;
-  // coefficient tables and the adjoint correlation exist for the FP64 instances only (compiled out of FP32)
+  // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
   constexpr bool kF64 = sizeof(T) == 8;
-  const bool use_tab = kF64 && A.coef != nullptr;
   const bool use_corr = kF64 && A.corr != nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit, s_abort;
@@ -226,6 +252,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   T *cs = red + (size_t)2 * C * W * NR * 32;         // [2][C][32][4]
   T *csh = cs + (size_t)2 * C * 32 * 4;              // [2][C][32]
   T *yup = csh + (size_t)2 * C * 32;                 // [W][APW][C][NS]
+  unsigned *csup = reinterpret_cast<unsigned *>(yup + (size_t)W * APW * C * NS);   // [2][C][32]
 
   if (threadIdx.x == 0) {
     s_unit = (int)atomicAdd(&A.ctrl[0], 1u);
@@ -239,14 +266,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   const int quad = pq / A.g.groups, grp = pq - quad * A.g.groups;
   const int sx = (quad == 0 || quad == 3) ? 1 : -1;
   const int sy = (quad <= 1) ? 1 : -1;
-  const T fsx = (T)sx, fsy = (T)sy, fsxy = (T)(sx * sy);
+  const unsigned mx = sx > 0 ? 0u : 0x80000000u, my = sy > 0 ? 0u : 0x80000000u, mxy = mx ^ my;
   const int gsize = (A.nq + A.g.groups - 1) / A.g.groups;
   const int g0 = grp * gsize;
   const int gcount = min(gsize, A.nq - g0);
+  const T c23 = (T)(2.0 / 3.0), c29 = (T)(2.0 / 9.0);
 
+  // per-direction constants (signs of the quadrant folded in: the reduction is in the global frame)
   int ang[APW], uA[APW], cA[APW], kA[APW];
-  T wA[APW], aA[APW], bA[APW];
+  T wA[APW], aA[APW], bA[APW], c2a[APW], c2b[APW];
+  T Wx[APW], Wy[APW];                 // w sx (2a, ...) / w sy (2b, ...): face terms of u0 (LM, RLM); w sx, w sy (STD)
+  T Dx[APW], Dy[APW], nWxb[APW], nWya[APW], W3a[APW], W3b[APW], wx[APW], wy[APW];   // RLMDG; W3*: w sx sy (STD)
   int nA = 0;
+  T Ga = 0, Gb = 0;                   // LMDG: sum over the warp's directions of w 2/3 a, w 2/3 b
 #pragma unroll
   for (int k = 0; k < APW; ++k) {
     const int idx = warp + k * W;
@@ -254,23 +286,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     if (idx < gcount) nA = k + 1;
     uA[k] = A.perm[ang[k]];
     cA[k] = (kF64 && A.corr) ? A.rev[ang[k]] : 0;
-    kA[k] = (kF64 && A.coef) ? A.cls[ang[k]] : 0;
-    wA[k] = A.pd.w[ang[k]];
-    aA[k] = fabs(A.pd.ox[ang[k]]);
-    bA[k] = fabs(A.pd.oy[ang[k]]);
+    kA[k] = TAB ? A.cls[ang[k]] * NC : 0;
+    const T w = A.pd.w[ang[k]], a = fabs(A.pd.ox[ang[k]]), b = fabs(A.pd.oy[ang[k]]);
+    wA[k] = w; aA[k] = a; bA[k] = b;
+    c2a[k] = 2 * a; c2b[k] = 2 * b;
+    if (VAR == 0) {
+      Wx[k] = flip(w, mx); Wy[k] = flip(w, my); W3a[k] = flip(w, mxy);
+    } else {
+      Wx[k] = flip(2 * w * a, mx); Wy[k] = flip(2 * w * b, my);
+      if (idx < gcount) { Ga += w * c23 * a; Gb += w * c23 * b; }
+    }
+    if (VAR == 2) {
+      Dx[k] = flip(w * (2 * a + c23 * b), mx); Dy[k] = flip(w * (2 * b + c23 * a), my);
+      nWxb[k] = flip(w * c23 * b, mx ^ 0x80000000u); nWya[k] = flip(w * c23 * a, my ^ 0x80000000u);
+      W3a[k] = flip(w * c23 * a, mxy); W3b[k] = flip(w * c23 * b, mxy);
+      wx[k] = flip(w, mx); wy[k] = flip(w, my);
+    }
   }
+  // LMDG slope-trace terms, per lane: -sx Gb V1 (r = 1), -sy Ga U1 (r = 2), sx sy (Ga U1 + Gb V1) (r = 3)
+  const T nGb = flip(Gb, mx ^ 0x80000000u), nGa = flip(Ga, my ^ 0x80000000u);
+  const T G3a = flip(Ga, mxy), G3b = flip(Gb, mxy);
 
   const int row = strip * 32 + lane;
   const bool row_ok = row < n;
   const int j = sy > 0 ? row : n - 1 - row;
   const T h = A.h;
-  const T c23 = (T)(2.0 / 3.0), c29 = (T)(2.0 / 9.0);
+  const double *tab = TAB ? A.coef : nullptr;
+  const int tab_stride = TAB ? A.ncls * NC : 0;
 
+  // upwind state: xs = this lane's previous cell (the left neighbour), ys = what goes to the cell above
+  //   STD: (U0, U1) / (V0, V1) outflow traces;  LM: mean traces (U0 / V0) per direction, the slope traces per
+  //   lane (xl1 / yl1);  RLM: (U0, U1, u0) / (V0, V1, u0) per direction
   T xs[APW][NS], ys[APW][NS];
 #pragma unroll
   for (int k = 0; k < APW; ++k)
 #pragma unroll
     for (int c = 0; c < NS; ++c) xs[k][c] = ys[k][c] = (T)0;
+  T xl1 = 0, yl1 = 0;
 
   const bool has_above = strip + 1 < A.g.strips;
   // upstream trace entry of item it = (direction k, step s, component c) of the chunk starting at t0
@@ -307,6 +359,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         const size_t K = (size_t)jj * n + ii;
         copy_cell<T>(cs + ((size_t)(b * C + s) * 32 + l) * 4, csh + (size_t)(b * C + s) * 32 + l,
                      A.cellsrc + 4 * K, A.cellsh + K);
+        if (VAR == 2 && A.supp) cp_async4(csup + (size_t)(b * C + s) * 32 + l, A.supp + K);
       }
     }
     cp_async_commit();
@@ -315,6 +368,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   stage(0);
   cp_async_wait_all();
   __syncthreads();
+
+  const bool src_bnd = A.source && A.pd.alpha;
 
   for (int cc = 0; cc < nchunks; ++cc) {
     const int t0 = cc * C;
@@ -361,9 +416,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
 
     // ---- C steps of the diagonal pipeline
     if (!wabort) {
-#ifdef LMDG_STEP_UNROLL
-#pragma unroll LMDG_STEP_UNROLL
-#endif
       for (int s = 0; s < C; ++s) {
         const int t = t0 + s;
         if (t >= nsteps) break;
@@ -373,68 +425,88 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         const int K = act ? j * n + i : 0;
         const bool xbnd = (x == 0);
         const bool ybnd = (strip == 0 && lane == 0);
+        const T *yws = yup + ((size_t)warp * APW * C + s) * NS;   // + k * C * NS: direction k's inflow (lane 0)
         // per-cell data in local coordinates
         const T *cp4 = cs + ((size_t)(b * C + s) * 32 + lane) * 4;
-        T sl[4] = {cp4[0], cp4[1], cp4[2], cp4[3]};
+        const T S0 = cp4[0], A1 = flip(cp4[1], mx), A2 = flip(cp4[2], my), A3 = flip(cp4[3], mxy);
         const T st = csh[(size_t)(b * C + s) * 32 + lane];
-        sl[1] *= fsx; sl[2] *= fsy; sl[3] *= fsxy;
+        // RLMDG: upwind faces without reconstruction (the upwind side is west / south in the local frame)
+        bool xsup = false, ysup = false;
+        if (VAR == 2 && A.supp && act) {
+          const unsigned mk = csup[(size_t)(b * C + s) * 32 + lane];
+          xsup = (mk & (sx > 0 ? 1u : 2u)) != 0;
+          ysup = (mk & (sy > 0 ? 4u : 8u)) != 0;
+        }
+        const double *cf = TAB ? tab + (size_t)mat_of(st) * tab_stride : nullptr;
 
         T acc[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] = 0;
 
+        // LMDG: the slope traces from below (one per lane; every direction carries the same value)
+        T yl1_in = 0;
+        if (VAR == 1) {
+          yl1_in = __shfl_up_sync(kFull, yl1, 1);
+          if (lane == 0) yl1_in = (ybnd || nA == 0) ? (T)0 : yws[1];
+        }
+        const T A13 = A1 + A3, A23 = A2 + A3;
+
 #pragma unroll
         for (int k = 0; k < APW; ++k) {
           if (k < nA) {
+            // inflow from the cell below (LMDG: the mean trace only; its slope trace is per lane)
+            constexpr int NSH = VAR == 1 ? 1 : NS;
             T yin[NS];
 #pragma unroll
-            for (int c = 0; c < NS; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
+            for (int c = 0; c < NSH; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
             if (act) {
-              if (lane == 0 && !ybnd) {
-                const T *yw = yup + (((size_t)warp * APW + k) * C + s) * NS;
+              if (lane == 0) {
 #pragma unroll
-                for (int c = 0; c < NS; ++c) yin[c] = yw[c];
+                for (int c = 0; c < NSH; ++c) yin[c] = ybnd ? (T)0 : yws[(size_t)k * C * NS + c];
               }
               const T a = aA[k], bb = bA[k], wl = wA[k];
+              // inflow boundary data (source sweeps): left face on x == 0, bottom face on the first row
               T xa0 = 0, xa1 = 0, ya0 = 0, ya1 = 0;
-              if (A.source && A.pd.alpha) {
+              if (src_bnd) {
                 if (xbnd) {
                   const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sx > 0 ? 0 : 1)) * n + j) * 2);
                   xa0 = ap[0];
-                  xa1 = fsy * ap[1];
+                  xa1 = flip(ap[1], my);
                 }
                 if (ybnd) {
                   const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sy > 0 ? 2 : 3)) * n + i) * 2);
                   ya0 = ap[0];
-                  ya1 = fsx * ap[1];
+                  ya1 = flip(ap[1], mx);
                 }
               }
-              T sa[4] = {sl[0], sl[1], sl[2], sl[3]};
+              T S = S0;
+              const T *qp = nullptr;
               if (A.source && A.q_per_angle) {
-                const T *qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
-                const T eps = A.eps;
-                sa[0] += 2 * h * eps * qp[0];
-                if (VAR == 0) {
-                  sa[1] += fsx * (2 * h / 3) * eps * qp[1];
-                  sa[2] += fsy * (2 * h / 3) * eps * qp[2];
-                  sa[3] += fsxy * (2 * h / 9) * eps * qp[3];
-                }
+                qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
+                S += 2 * h * A.eps * qp[0];
               }
               if (VAR == 0) {
-                // ---------------- standard Q1 block solve
-                const T U0 = xbnd ? xa0 : xs[k][0], U1 = xbnd ? xa1 : xs[k][1];
-                const T V0 = ybnd ? ya0 : yin[0], V1 = ybnd ? ya1 : yin[1];
-                const T r0 = sa[0] + 2 * a * U0 + 2 * bb * V0;
-                const T r1 = sa[1] - 2 * a * U0 + c23 * bb * V1;
-                const T r2 = sa[2] + c23 * a * U1 - 2 * bb * V0;
-                const T r3 = sa[3] - c23 * a * U1 - c23 * bb * V1;
+                // ---------------- standard Q1 block solve; inflow traces vanish outside the mesh
+                T sa1 = A1, sa2 = A2, sa3 = A3;
+                if (qp) {
+                  const T e = A.eps;
+                  sa1 += flip((2 * h / 3) * e * qp[1], mx);
+                  sa2 += flip((2 * h / 3) * e * qp[2], my);
+                  sa3 += flip((2 * h / 9) * e * qp[3], mxy);
+                }
+                const T U0 = xs[k][0] + xa0, U1 = xs[k][1] + xa1;
+                const T V0 = yin[0] + ya0, V1 = yin[1] + ya1;
+                const T ca = c23 * a, cb = c23 * bb;
+                const T r0 = S + c2a[k] * U0 + c2b[k] * V0;
+                const T r1 = sa1 - c2a[k] * U0 + cb * V1;
+                const T r2 = sa2 + ca * U1 - c2b[k] * V0;
+                const T r3 = sa3 - ca * U1 - cb * V1;
                 T u0, u1, u2, u3;
-                if (use_tab) {
-                  // table: the material index travels in the staged sigma_t h slot
-                  const double *cf = A.coef + ((size_t)(int)st * A.ncls + kA[k]) * 9;
-                  const T i1 = (T)__ldg(cf), i2 = (T)__ldg(cf + 1), p1 = (T)__ldg(cf + 2), p2 = (T)__ldg(cf + 3);
-                  const T q1 = (T)__ldg(cf + 4), q2 = (T)__ldg(cf + 5), e0 = (T)__ldg(cf + 6), e1 = (T)__ldg(cf + 7);
-                  const T e3 = (T)__ldg(cf + 8);
+                if (TAB) {
+                  const double *cfk = cf + kA[k];
+                  const T i1 = (T)__ldg(cfk), i2 = (T)__ldg(cfk + 1), p1 = (T)__ldg(cfk + 2), p2 = (T)__ldg(cfk + 3);
+                  const T q1 = (T)__ldg(cfk + 4), q2 = (T)__ldg(cfk + 5), e0 = (T)__ldg(cfk + 6), e1 = (T)__ldg(cfk + 7);
+                  const T e3 = (T)__ldg(cfk + 8);
                   const T b0 = r0 - p1 * r1 - p2 * r2;
                   const T b3 = r3 + q1 * r1 + q2 * r2;
                   u0 = e0 * b0 - e1 * b3;
@@ -463,74 +535,73 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   // stored forward psi of that opposite direction, per Legendre moment
                   const double *pf = A.corr + ((size_t)cA[k] * nx + K) * 4;
                   acc[0] += wl * u0 * (T)pf[0];
-                  acc[1] += wl * fsx * u1 * (T)pf[1];
-                  acc[2] += wl * fsy * u2 * (T)pf[2];
-                  acc[3] += wl * fsxy * u3 * (T)pf[3];
+                  acc[1] += Wx[k] * u1 * (T)pf[1];
+                  acc[2] += Wy[k] * u2 * (T)pf[2];
+                  acc[3] += W3a[k] * u3 * (T)pf[3];
                 } else {
                   acc[0] += wl * u0;
-                  acc[1] += wl * fsx * u1;
-                  acc[2] += wl * fsy * u2;
-                  acc[3] += wl * fsxy * u3;
+                  acc[1] += Wx[k] * u1;
+                  acc[2] += Wy[k] * u2;
+                  acc[3] += W3a[k] * u3;
                 }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
                 if (A.psi) {
                   T *pp = reinterpret_cast<T *>(A.psi) + ((size_t)uA[k] * nx + K) * 4;
-                  pp[0] = u0; pp[1] = fsx * u1; pp[2] = fsy * u2; pp[3] = fsxy * u3;
+                  pp[0] = u0; pp[1] = flip(u1, mx); pp[2] = flip(u2, my); pp[3] = flip(u3, mxy);
                 }
-              } else {
-                // ---------------- low-memory row-0 solve (L00, or Ltilde00 with reconstruction)
-                const T U0s = xbnd ? xa0 : xs[k][0];
-                const T V0s = ybnd ? ya0 : yin[0];
-                // sigma_t h and the coefficient row (table mode: st is the material index)
-                T sh = st, inv = 0, d1, d2, d3;
-                if (use_tab) {
-                  const double *cf = A.coef + ((size_t)(int)st * A.ncls + kA[k]) * 4;
-                  inv = (T)__ldg(cf); d1 = (T)__ldg(cf + 1); d2 = (T)__ldg(cf + 2); d3 = (T)__ldg(cf + 3);
-                  sh = (T)__ldg(A.matsh + (int)st);
-                } else {
-                  d1 = 2 * a + c23 * (bb + sh);
-                  d2 = 2 * bb + c23 * (a + sh);
-                  d3 = c23 * (a + bb) + c29 * sh;
-                }
-                const T d0 = 2 * (a + bb + sh);
-                T rhs = sa[0] + 2 * a * (U0s - sa[1]) + 2 * bb * (V0s - sa[2]);
-                T u0, rec1 = 0, rec2 = 0;
-                if (VAR == 1) {
-                  u0 = rhs * (use_tab ? inv : rcp(d0));
-                } else {
-                  // reconstructed slopes (h/2) delta: interior (u0 - u0_up)/2, inflow boundary u0 - alpha_mid
-                  const T cx = xbnd ? 2 * a : a, cy = ybnd ? 2 * bb : bb;
-                  rhs += xbnd ? 2 * a * xa0 : a * xs[k][NS - 1];
-                  rhs += ybnd ? 2 * bb * ya0 : bb * yin[NS - 1];
-                  u0 = rhs * ((use_tab && !xbnd && !ybnd) ? inv : rcp(d0 + cx + cy));
-                  rec1 = xbnd ? (u0 - xa0) : (T)0.5 * (u0 - xs[k][NS - 1]);
-                  rec2 = ybnd ? (u0 - ya0) : (T)0.5 * (u0 - yin[NS - 1]);
-                }
-                const T u1 = sa[1] + rec1, u2 = sa[2] + rec2, u3 = sa[3];
-                // rows 1..3 of L applied to the trial function (inflow traces of L vanish on the boundary)
-                const T U0L = xbnd ? (T)0 : xs[k][0], U1L = xbnd ? (T)0 : xs[k][1];
-                const T V0L = ybnd ? (T)0 : yin[0], V1L = ybnd ? (T)0 : yin[1];
-                const T T1 = -2 * a * u0 + d1 * u1 + c23 * bb * u3 + 2 * a * U0L - c23 * bb * V1L;
-                const T T2 = -2 * bb * u0 + d2 * u2 + c23 * a * u3 - c23 * a * U1L + 2 * bb * V0L;
-                const T T3 = -c23 * bb * u1 - c23 * a * u2 + d3 * u3 + c23 * (a * U1L + bb * V1L);
+              } else if (VAR == 1) {
+                // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
+                //   rhs = S + 2a (U0 - A1) + 2b (V0 - A2), U0 / V0 the mean inflow traces (alpha on the boundary)
+                const T U0 = xs[k][0], V0 = yin[0];
+                const T rhs = c2a[k] * (U0 + xa0 - A1) + (c2b[k] * (V0 + ya0 - A2) + S);
+                const T u0 = rhs * (TAB ? (T)__ldg(cf + kA[k]) : rcp(2 * (a + bb + st)));
+                // direction-dependent part of L(u; b_1), L(u; b_2): 2a (U0 - u0), 2b (V0 - u0) (zero inflow traces
+                // outside the mesh)
                 if (use_corr) {
-                  // adjoint correlation (low-memory): cell averages of this sweep (the multiplier of the opposite
-                  // direction) times the stored forward psi0 of that direction
                   acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
                 } else {
-                  acc[0] += wl * u0;
-                  acc[1] += wl * fsx * T1;
-                  acc[2] += wl * fsy * T2;
-                  acc[3] += wl * fsxy * T3;
+                  acc[0] = fma(wl, u0, acc[0]);
+                  acc[1] = fma(Wx[k], U0 - u0, acc[1]);
+                  acc[2] = fma(Wy[k], V0 - u0, acc[2]);
                 }
-                if (VAR == 2) {
-                  acc[NR - 2] += wl * fsx * rec1;
-                  acc[NR - 1] += wl * fsy * rec2;
+                xs[k][0] = u0 + A1;
+                ys[k][0] = u0 + A2;
+                ys[k][1] = A13;
+                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
+              } else {
+                // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
+                //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
+                //   a suppressed face; 2a (h/2) delta_x enters row 0 through L01
+                const T U0 = xs[k][0], U1 = xs[k][1], Ux = xs[k][2];
+                const T V0 = yin[0], V1 = yin[1], Vy = yin[2];
+                T rhs = c2a[k] * (U0 - A1) + (c2b[k] * (V0 - A2) + S);
+                rhs += a * (xsup ? (T)0 : Ux) + bb * (ysup ? (T)0 : Vy);
+                if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
+                const int bi = (xbnd ? 1 : (xsup ? 2 : 0)) + 3 * (ybnd ? 1 : (ysup ? 2 : 0));
+                const T inv = TAB ? (T)__ldg(cf + kA[k] + bi)
+                                  : rcp(2 * st + a * (T)(xbnd ? 4 : (xsup ? 2 : 3)) +
+                                        bb * (T)(ybnd ? 4 : (ysup ? 2 : 3)));
+                const T u0 = rhs * inv;
+                T rec1 = (xbnd ? (T)1 : (xsup ? (T)0 : (T)0.5)) * (u0 - Ux);
+                T rec2 = (ybnd ? (T)1 : (ysup ? (T)0 : (T)0.5)) * (u0 - Vy);
+                if (src_bnd) { rec1 -= xa0; rec2 -= ya0; }
+                // direction-dependent part of L(u; b_r): u1 = A1 + rec1, u2 = A2 + rec2, inflow traces U, V
+                //   r=1: 2a (U0 - u0) + (2a + 2/3 b) rec1 - 2/3 b V1   (2/3 sigma_t h rec1: epilogue)
+                //   r=2: 2b (V0 - u0) + (2b + 2/3 a) rec2 - 2/3 a U1
+                //   r=3: 2/3 a (U1 - rec2) + 2/3 b (V1 - rec1)
+                if (use_corr) {
+                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
+                } else {
+                  acc[0] = fma(wl, u0, acc[0]);
+                  acc[1] = fma(nWxb[k], V1, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
+                  acc[2] = fma(nWya[k], U1, fma(Dy[k], rec2, fma(Wy[k], V0 - u0, acc[2])));
+                  acc[3] = fma(W3b[k], V1 - rec1, fma(W3a[k], U1 - rec2, acc[3]));
                 }
-                xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
-                ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-                if (VAR == 2) { xs[k][NS - 1] = u0; ys[k][NS - 1] = u0; }
+                acc[4] = fma(wx[k], rec1, acc[4]);
+                acc[5] = fma(wy[k], rec2, acc[5]);
+                xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
+                ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
@@ -540,6 +611,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
               }
             }
           }
+        }
+        if (VAR == 1 && act) {
+          if (nA > 0 && !use_corr) {
+            // slope-trace terms, the same for every direction: -2/3 b V1 (r=1), -2/3 a U1 (r=2),
+            // 2/3 (a U1 + b V1) (r=3), U1 = the left cell's A2 + A3, V1 = the lower cell's A1 + A3
+            acc[1] += nGb * yl1_in;
+            acc[2] += nGa * xl1;
+            acc[3] += G3a * xl1 + G3b * yl1_in;
+          }
+          xl1 = A23;
+          yl1 = A13;
         }
         T *rb = red + ((size_t)((b * C + s) * W + warp) * NR) * 32 + lane;
 #pragma unroll
@@ -572,16 +654,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   }
 }
 
+// Quadrature moments used by the epilogue: [sum w, sum w |Omega_x|, sum w |Omega_y|, sum w Omega_x, sum w Omega_y]
+// over all directions, summed in index order.
+__global__ void quad_moments_kernel(int nang, const double *__restrict__ ox, const double *__restrict__ oy,
+                                    const double *__restrict__ w, double *__restrict__ qm) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double m[5] = {0, 0, 0, 0, 0};
+  for (int l = 0; l < nang; ++l) {
+    m[0] += w[l];
+    m[1] += w[l] * fabs(ox[l]);
+    m[2] += w[l] * fabs(oy[l]);
+    m[3] += w[l] * ox[l];
+    m[4] += w[l] * oy[l];
+  }
+  for (int r = 0; r < 5; ++r) qm[r] = m[r];
+}
+
 // y = K X - source * b from the partial reductions, one thread per cell.
 //   STD : y = X - sum_p part_p                       (K = I - P L^-1 M; b = P L^-1 Q)
 //   LM/RLM: y0 = X0 - P0 psi0
 //           y_r = (sigma_s/eps) h^2 D_r (S_r - source P1r_alpha_r - X_r) - (h/2) T_r + source SigmaQ1_r
 // where T_r = sum_l w_l L_l(u_l; b_r) over the full trial functions u_l = psi0_l + (R psi0)_l - X1 and S = P1 R
 // psi0.  For the homogeneous sweep this equals the second block row B11 X1 - (Sigma Ltilde10 + B11 P1 R) psi0
-// of the reduced operator, because Sigma L11 Sigma^T = B11 + Sigma M1 (eq-lmdg-psi1).
+// of the reduced operator, because Sigma L11 Sigma^T = B11 + Sigma M1 (eq-lmdg-psi1).  The partials hold the
+// direction-dependent part of T_r; the part through the cell's own isotropic slopes A_r = -(X_r + source
+// P1r_alpha_r) is added here with the quadrature moments qm (s = sigma_t h, c = 2/3):
+//   T_1 += (2 Ma + c Mb + c s Mw) A_1 + c MOy A_3 [+ c s sum w sx rec_1]
+//   T_2 += (2 Mb + c Ma + c s Mw) A_2 + c MOx A_3 [+ c s sum w sy rec_2]
+//   T_3 += -c MOy A_1 - c MOx A_2 + (c (Ma + Mb) + 2/9 s Mw) A_3
 template <typename T, int VAR>
 __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ part,
                                 const double *__restrict__ X, const double *__restrict__ sse,
+                                const double *__restrict__ sigt, const double *__restrict__ qm,
                                 const double *__restrict__ p1ra, const double *__restrict__ sq1, int source,
                                 double *__restrict__ y) {
   constexpr int NR = (VAR == 2) ? 6 : 4;
@@ -602,48 +706,65 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
     o0 = xa.x - s[0]; o1 = xa.y - s[1]; o2 = xb.x - s[2]; o3 = xb.y - s[3];
   } else {
     const double m = sse[K] * h * h;
-    double S1 = 0, S2 = 0;
+    const double c = 2.0 / 3.0, sh = sigt[K] * h;
+    const double Mw = qm[0], Ma = qm[1], Mb = qm[2], MOx = qm[3], MOy = qm[4];
+    double S1 = 0, S2 = 0, p1 = 0, p2 = 0;
     if (VAR == 2) {
       S1 = s[4]; S2 = s[5];
-      if (source && p1ra) { S1 -= p1ra[2 * (size_t)K]; S2 -= p1ra[2 * (size_t)K + 1]; }
+      if (source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; S1 -= p1; S2 -= p2; }
     }
+    const double A1 = -(xa.y + p1), A2 = -(xb.x + p2), A3 = -xb.y;
+    double T1 = s[1] + (2 * Ma + c * Mb + c * sh * Mw) * A1 + c * MOy * A3;
+    double T2 = s[2] + (2 * Mb + c * Ma + c * sh * Mw) * A2 + c * MOx * A3;
+    const double T3 = s[3] - c * MOy * A1 - c * MOx * A2 + (c * (Ma + Mb) + (2.0 / 9.0) * sh * Mw) * A3;
+    if (VAR == 2) { T1 += c * sh * s[4]; T2 += c * sh * s[5]; }
     o0 = xa.x - s[0];
-    o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * s[1];
-    o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * s[2];
-    o3 = m * (1.0 / 9.0) * (0.0 - xb.y) - 0.5 * h * s[3];
+    o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * T1;
+    o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * T2;
+    o3 = m * (1.0 / 9.0) * (0.0 - xb.y) - 0.5 * h * T3;
     if (source && sq1) { o1 += sq1[3 * (size_t)K]; o2 += sq1[3 * (size_t)K + 1]; o3 += sq1[3 * (size_t)K + 2]; }
   }
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K) = make_double2(o0, o1);
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(o2, o3);
 }
 
-template <typename T, int VAR, int APW>
+template <typename T, int VAR, int APW, bool TAB>
 static const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW>);
+  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW, TAB>);
 }
 
-template <typename T, int VAR>
+template <typename T, int VAR, bool TAB>
 static const void *kernel_for(int apw) {
   switch (apw) {
-    case 1: return kernel_ptr<T, VAR, 1>();
-    case 2: return kernel_ptr<T, VAR, 2>();
-    case 3: return kernel_ptr<T, VAR, 3>();
-    default: return kernel_ptr<T, VAR, 4>();
+    case 1: return kernel_ptr<T, VAR, 1, TAB>();
+    case 2: return kernel_ptr<T, VAR, 2, TAB>();
+    case 3: return kernel_ptr<T, VAR, 3, TAB>();
+    default: return kernel_ptr<T, VAR, 4, TAB>();
   }
 }
 
-template <typename T>
-static const void *sweep_kernel_ptr(int variant, int apw) {
+template <typename T, bool TAB>
+static const void *kernel_for_variant(int variant, int apw) {
   switch (variant) {
-    case LMDG_STD: return kernel_for<T, 0>(apw);
-    case LMDG_LM: return kernel_for<T, 1>(apw);
-    default: return kernel_for<T, 2>(apw);
+    case LMDG_STD: return kernel_for<T, 0, TAB>(apw);
+    case LMDG_LM: return kernel_for<T, 1, TAB>(apw);
+    default: return kernel_for<T, 2, TAB>(apw);
   }
+}
+
+// coefficient tables are an FP64 feature: the FP32 instances always form the coefficients themselves
+template <typename T>
+static const void *sweep_kernel_ptr(int variant, int apw, bool tab) {
+  if constexpr (sizeof(T) == 8) {
+    if (tab) return kernel_for_variant<T, true>(variant, apw);
+  }
+  (void)tab;
+  return kernel_for_variant<T, false>(variant, apw);
 }
 
 template <typename T>
 int sweep_blocks_per_sm(int variant, int warps, int apw) {
-  const void *k = sweep_kernel_ptr<T>(variant, apw);
+  const void *k = sweep_kernel_ptr<T>(variant, apw, false);
   const size_t smem = sweep_smem_bytes<T>(variant, warps, apw);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
@@ -676,7 +797,7 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   }
   cudaError_t e = cudaMemsetAsync(a.ctrl, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw);
+  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr);
   const size_t smem = sweep_smem_bytes<T>(variant, a.g.warps, a.g.apw);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -688,17 +809,28 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t quad_moments(int nang, const double *ox, const double *oy, const double *w, double *qm, cudaStream_t s) {
+  add_launches(1);
+  quad_moments_kernel<<<1, 32, 0, s>>>(nang, ox, oy, w, qm);
+  return cudaGetLastError();
+}
+
 template <typename T>
-cudaError_t launch_epilogue(int variant, int n, int nx, int P, double h, const T *part, const double *X,
-                            const double *sse, const double *p1ra, const double *sq1, int source, double *y,
-                            cudaStream_t s) {
-  (void)n;
+cudaError_t launch_epilogue(int variant, int nx, int P, double h, const T *part, const double *X,
+                            const double *sse, const double *sigt, const double *qm, const double *p1ra,
+                            const double *sq1, int source, double *y, cudaStream_t s) {
   const int bs = 256, gs = (nx + bs - 1) / bs;
   add_launches(1);
   switch (variant) {
-    case LMDG_STD: epilogue_kernel<T, 0><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, p1ra, sq1, source, y); break;
-    case LMDG_LM: epilogue_kernel<T, 1><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, p1ra, sq1, source, y); break;
-    default: epilogue_kernel<T, 2><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, p1ra, sq1, source, y); break;
+    case LMDG_STD:
+      epilogue_kernel<T, 0><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
+      break;
+    case LMDG_LM:
+      epilogue_kernel<T, 1><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
+      break;
+    default:
+      epilogue_kernel<T, 2><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
+      break;
   }
   return cudaGetLastError();
 }
@@ -709,11 +841,11 @@ template int sweep_blocks_per_sm<double>(int, int, int);
 template int sweep_blocks_per_sm<float>(int, int, int);
 template cudaError_t launch_sweep<double>(int, const SweepArgs<double> &, cudaStream_t);
 template cudaError_t launch_sweep<float>(int, const SweepArgs<float> &, cudaStream_t);
-template cudaError_t launch_epilogue<double>(int, int, int, int, double, const double *, const double *,
-                                             const double *, const double *, const double *, int, double *,
-                                             cudaStream_t);
-template cudaError_t launch_epilogue<float>(int, int, int, int, double, const float *, const double *,
-                                            const double *, const double *, const double *, int, double *,
-                                            cudaStream_t);
+template cudaError_t launch_epilogue<double>(int, int, int, double, const double *, const double *, const double *,
+                                             const double *, const double *, const double *, const double *, int,
+                                             double *, cudaStream_t);
+template cudaError_t launch_epilogue<float>(int, int, int, double, const float *, const double *, const double *,
+                                            const double *, const double *, const double *, const double *, int,
+                                            double *, cudaStream_t);
 
 }  // namespace lmdg

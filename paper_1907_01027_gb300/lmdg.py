@@ -34,7 +34,8 @@ class Quad(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("precond", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("device", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("device", ctypes.c_int),
+                ("suppress", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

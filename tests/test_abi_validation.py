@@ -65,3 +65,20 @@ def test_valid_arguments_reach_the_device(L):
         pytest.skip("valid setup is exercised by the GPU tests")
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
     assert _setup(L, p) == -4                                  # validated, then no CUDA device here
+
+
+def test_suppress_option_validated(L):
+    """The suppression switch is RLMDG's only and takes 0 or 1."""
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
+    quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+    for variant, flag in ((0, 1), (1, 1), (2, 2), (2, -1)):
+        o = Options()
+        L.lmdg_default_options(ctypes.byref(o))
+        o.suppress = flag
+        h = ctypes.c_void_p()
+        rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
+        assert rc == -1, (variant, flag)
