@@ -31,6 +31,12 @@ VARIANTS = ("std", "lm", "rlm")
 # reciprocals count 1): standard Q1 block solve, low-memory row-0 solve + L-row reductions, reconstructed.
 FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 
+# DRAM bytes (read + write) per launch of the FP32 non-storing sweep kernel, from one ncu capture of the
+# 512x512 S16 profiling case (bench.py --profile); the launch shape, hence the partial reductions per cell, is
+# the same at 1024x1024, so a full launch moves 4x these.  Must be re-measured whenever the kernel changes.
+SWEEP_DRAM_BYTES_512 = {"std": 18.665984e6 + 40.936960e6, "lm": 18.561024e6 + 9.046528e6,
+                        "rlm": 16.137216e6 + 82.065152e6}
+
 
 def workload_config():
     return {"workload": "1024x1024 cells, S16 level-symmetric (144 directions), sigma_s and sigma_a piecewise "
@@ -233,9 +239,14 @@ def run_gpu(args, rank, ws, dist):
     flops = sum(FLOPS_PER_UPDATE[v] * st["sweeps_fp32"] * upd for v, st in stats)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = flops / (f32_ms / 1e3) / 1e12 if f32_ms > 0 else None
+    scale = (p.n / 512) ** 2
+    traffic = sum(SWEEP_DRAM_BYTES_512[v] * scale * st["sweeps_fp32"] for v, st in stats) / max(1, f32_n)
     roofline = {"bound": "alu", "kernel": "sweep_kernel<float> (all three schemes, non-storing)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 512x512 profiling "
+                                  "case, per scheme, scaled by the cell count and averaged over the timed "
+                                  "launches (profiles/sweep_kernels_512x512_S16.md)",
                 "peak_source": "FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                 "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n,
                 "flops_per_update": FLOPS_PER_UPDATE,
@@ -330,9 +341,10 @@ def run_gpu(args, rank, ws, dist):
 
 
 def run_profile(args):
-    """Small case for ncu: 512x512 cells, S16, the bench media; per round an FP32 LMDG sweep (non-storing), an
-    FP32 Q1-DG storing sweep (psi 604 MB, larger than L2) and FP64 Q1-DG, LMDG and RLMDG sweeps (as in the
-    refinement residual); two rounds (sweep kernels 1-5 untimed, 6-10 for the capture)."""
+    """Small case for ncu: 512x512 cells, S16, the bench media; per round the three FP32 non-storing sweeps (as
+    inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2) and the three
+    FP64 source sweeps (as in the refinement residual); two rounds (sweep kernels 1-7 untimed, 8-14 for the
+    capture)."""
     import torch
     from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
     from workloads.problems import config4
@@ -342,7 +354,8 @@ def run_profile(args):
     x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(2):
-        ctx["lm"].sweep(x, y, flags=SWEEP_FP32)
+        for v in ("std", "lm", "rlm"):
+            ctx[v].sweep(x, y, flags=SWEEP_FP32)
         ctx["std"].sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
         for v in ("std", "lm", "rlm"):
             ctx[v].sweep(x, y, flags=SWEEP_SOURCE)
