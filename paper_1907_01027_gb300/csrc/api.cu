@@ -82,6 +82,8 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   if constexpr (sizeof(T) == 8) a.corr = c->corr;
   a.supp = c->supp;
   a.coef = nullptr; a.ncoef = 0; a.ncls = 0; a.cls = nullptr; a.matsh = nullptr; a.mat = nullptr;
+  // coefficient tables for the FP64 sweeps, where they replace FP64 reciprocals; the FP32 sweeps form the
+  // coefficients with the hardware reciprocal as fast as they would load them (measured at 1024^2 S16)
   if constexpr (sizeof(T) == 8) {
     if (c->coef) {
       a.coef = c->coef; a.ncoef = c->ncoef; a.ncls = c->ncls; a.cls = c->cls; a.matsh = c->matsh; a.mat = c->mat;

@@ -57,10 +57,10 @@ struct SweepArgs {
   const double *corr;  // adjoint correlation mode: stored forward psi ([nang(user)][nx][4] standard, [nang][nx]
                        // low-memory); the reduction becomes sum_l w_l u_l,r psi_rev(l),r (r = 0 only for LMDG)
   const int *rev;      // [nang] sorted index -> user index of the opposite direction (corr mode)
-  // FP64 coefficient tables (null: coefficients computed in the kernel).  With them, cellsh carries the cell's
-  // material index and coef[(material * ncls + class) * ncoef + c] the solve coefficients of that material
-  // (sigma_t h) and direction class (|Omega_x|, |Omega_y|).
-  const double *coef;
+  // Coefficient tables (FP64 sweeps; null: coefficients computed in the kernel).  With them, cellsh carries the
+  // cell's material index and coef[(material * ncls + class) * ncoef + c] the solve coefficients of that
+  // material (sigma_t h) and direction class (|Omega_x|, |Omega_y|).
+  const T *coef;
   int ncoef, ncls;
   const int *cls;      // [nang] sorted index -> direction class
   const double *matsh; // [materials] sigma_t h of each material

@@ -54,7 +54,13 @@ __device__ __forceinline__ double rcp(double x) {
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
 }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// FP32 sweeps (the inner solves of the refinement) take the hardware reciprocal approximation (rcp.approx, about
+// one ulp) instead of the correctly rounded one.
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
   unsigned v;
@@ -88,6 +94,42 @@ template <> __device__ __forceinline__ void copy_cell<double>(double *d4, double
   cp_async16(d4, s4);
   cp_async16(d4 + 2, s4 + 2);
   cp_async8(dh, sh);
+}
+
+// NR consecutive values (a cell's reduced moments) moved with the widest aligned vector accesses: the buffers
+// hold them at NR-element strides, so NR = 4 floats are 16-byte aligned, NR = 6 floats 8-byte aligned and
+// doubles 16-byte aligned.
+template <typename T, int NR> __device__ __forceinline__ void store_nr(T *dst, const T *v) {
+  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 4) *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2) {
+      if constexpr (sizeof(T) == 4) *reinterpret_cast<float2 *>(dst + q) = make_float2(v[q], v[q + 1]);
+      else *reinterpret_cast<double2 *>(dst + q) = make_double2(v[q], v[q + 1]);
+    }
+  }
+}
+template <typename T, int NR> __device__ __forceinline__ void add_nr(T *acc, const T *src) {
+  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(src + q);
+      acc[q] += t.x; acc[q + 1] += t.y; acc[q + 2] += t.z; acc[q + 3] += t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2) {
+      if constexpr (sizeof(T) == 4) {
+        const float2 t = *reinterpret_cast<const float2 *>(src + q);
+        acc[q] += t.x; acc[q + 1] += t.y;
+      } else {
+        const double2 t = *reinterpret_cast<const double2 *>(src + q);
+        acc[q] += t.x; acc[q + 1] += t.y;
+      }
+    }
+  }
 }
 
 template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size_t idx, T v, int bf16) {
@@ -134,7 +176,7 @@ __device__ __forceinline__ int mat_of(float v) { return __float_as_int(v); }
 
 }  // namespace
 
-// Shared-memory bytes of one CTA: partial reductions [2][kChunk][W][NR][32], cell data [2][kChunk][32][4] and
+// Shared-memory bytes of one CTA: partial reductions [2][kChunk][W][32][NR], cell data [2][kChunk][32][4] and
 // [2][kChunk][32], upstream traces [W][APW][kChunk][NS], RLMDG suppression bits [2][kChunk][32].
 template <typename T>
 size_t sweep_smem_bytes(int variant, int warps, int apw) {
@@ -231,8 +273,8 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 #define LMDG_MINB32 2
 #endif
 
-// TAB: the element-solve coefficients come from the FP64 tables (FP64 instances only), else they are formed in
-// the kernel from sigma_t h.
+// TAB: the element-solve coefficients come from the FP64 tables (per material and direction class; FP64
+// instances only), else they are formed in the kernel from sigma_t h.
 template <typename T, int VAR, int APW, bool TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr int NR = (VAR == 2) ? 6 : 4;   // reduced values per cell
@@ -248,7 +290,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int W = A.g.warps;
   const int n = A.n, nx = A.nx;
-  T *red = reinterpret_cast<T *>(smem_raw);          // [2][C][W][NR][32]
+  T *red = reinterpret_cast<T *>(smem_raw);          // [2][C][W][32][NR]
   T *cs = red + (size_t)2 * C * W * NR * 32;         // [2][C][32][4]
   T *csh = cs + (size_t)2 * C * 32 * 4;              // [2][C][32]
   T *yup = csh + (size_t)2 * C * 32;                 // [W][APW][C][NS]
@@ -274,7 +316,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
 
   // per-direction constants (signs of the quadrant folded in: the reduction is in the global frame)
   int ang[APW], uA[APW], cA[APW], kA[APW];
-  T wA[APW], aA[APW], bA[APW], c2a[APW], c2b[APW];
+  T wA[APW], aA[APW], bA[APW], c2a[APW], c2b[APW], c23a[APW], c23b[APW];
   T Wx[APW], Wy[APW];                 // w sx (2a, ...) / w sy (2b, ...): face terms of u0 (LM, RLM); w sx, w sy (STD)
   T Dx[APW], Dy[APW], nWxb[APW], nWya[APW], W3a[APW], W3b[APW], wx[APW], wy[APW];   // RLMDG; W3*: w sx sy (STD)
   int nA = 0;
@@ -289,7 +331,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     kA[k] = TAB ? A.cls[ang[k]] * NC : 0;
     const T w = A.pd.w[ang[k]], a = fabs(A.pd.ox[ang[k]]), b = fabs(A.pd.oy[ang[k]]);
     wA[k] = w; aA[k] = a; bA[k] = b;
-    c2a[k] = 2 * a; c2b[k] = 2 * b;
+    c2a[k] = 2 * a; c2b[k] = 2 * b; c23a[k] = c23 * a; c23b[k] = c23 * b;
     if (VAR == 0) {
       Wx[k] = flip(w, mx); Wy[k] = flip(w, my); W3a[k] = flip(w, mxy);
     } else {
@@ -311,7 +353,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   const bool row_ok = row < n;
   const int j = sy > 0 ? row : n - 1 - row;
   const T h = A.h;
-  const double *tab = TAB ? A.coef : nullptr;
+  const T *tab = TAB ? A.coef : nullptr;
   const int tab_stride = TAB ? A.ncls * NC : 0;
 
   // upwind state: xs = this lane's previous cell (the left neighbour), ys = what goes to the cell above
@@ -437,7 +479,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
           xsup = (mk & (sx > 0 ? 1u : 2u)) != 0;
           ysup = (mk & (sy > 0 ? 4u : 8u)) != 0;
         }
-        const double *cf = TAB ? tab + (size_t)mat_of(st) * tab_stride : nullptr;
+        const T *cf = TAB ? tab + (size_t)mat_of(st) * tab_stride : nullptr;
 
         T acc[NR];
 #pragma unroll
@@ -494,16 +536,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   sa2 += flip((2 * h / 3) * e * qp[2], my);
                   sa3 += flip((2 * h / 9) * e * qp[3], mxy);
                 }
-                const T U0 = xs[k][0] + xa0, U1 = xs[k][1] + xa1;
-                const T V0 = yin[0] + ya0, V1 = yin[1] + ya1;
-                const T ca = c23 * a, cb = c23 * bb;
+                T U0 = xs[k][0], U1 = xs[k][1], V0 = yin[0], V1 = yin[1];
+                if (src_bnd) { U0 += xa0; U1 += xa1; V0 += ya0; V1 += ya1; }
+                const T ca = c23a[k], cb = c23b[k];
                 const T r0 = S + c2a[k] * U0 + c2b[k] * V0;
                 const T r1 = sa1 - c2a[k] * U0 + cb * V1;
                 const T r2 = sa2 + ca * U1 - c2b[k] * V0;
                 const T r3 = sa3 - ca * U1 - cb * V1;
                 T u0, u1, u2, u3;
                 if (TAB) {
-                  const double *cfk = cf + kA[k];
+                  const T *cfk = cf + kA[k];
                   const T i1 = (T)__ldg(cfk), i2 = (T)__ldg(cfk + 1), p1 = (T)__ldg(cfk + 2), p2 = (T)__ldg(cfk + 3);
                   const T q1 = (T)__ldg(cfk + 4), q2 = (T)__ldg(cfk + 5), e0 = (T)__ldg(cfk + 6), e1 = (T)__ldg(cfk + 7);
                   const T e3 = (T)__ldg(cfk + 8);
@@ -554,7 +596,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
                 //   rhs = S + 2a (U0 - A1) + 2b (V0 - A2), U0 / V0 the mean inflow traces (alpha on the boundary)
                 const T U0 = xs[k][0], V0 = yin[0];
-                const T rhs = c2a[k] * (U0 + xa0 - A1) + (c2b[k] * (V0 + ya0 - A2) + S);
+                T rhs = c2a[k] * (U0 - A1) + (c2b[k] * (V0 - A2) + S);
+                if (src_bnd) rhs += c2a[k] * xa0 + c2b[k] * ya0;
                 const T u0 = rhs * (TAB ? (T)__ldg(cf + kA[k]) : rcp(2 * (a + bb + st)));
                 // direction-dependent part of L(u; b_1), L(u; b_2): 2a (U0 - u0), 2b (V0 - u0) (zero inflow traces
                 // outside the mesh)
@@ -623,9 +666,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
           xl1 = A23;
           yl1 = A13;
         }
-        T *rb = red + ((size_t)((b * C + s) * W + warp) * NR) * 32 + lane;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) rb[r * 32] = acc[r];
+        store_nr<T, NR>(red + ((size_t)((b * C + s) * W + warp) * 32 + lane) * NR, acc);
       }
     }
 
@@ -643,13 +684,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
 #pragma unroll
       for (int q = 0; q < NR; ++q) sum[q] = 0;
       for (int ww = 0; ww < W; ++ww) {
-        const T *src = red + ((size_t)((b * C + s) * W + ww) * NR) * 32 + l;
-#pragma unroll
-        for (int q = 0; q < NR; ++q) sum[q] += src[q * 32];
+        add_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W + ww) * 32 + l) * NR);
       }
       T *dst = A.part + ((size_t)pq * nx + K) * NR;
-#pragma unroll
-      for (int q = 0; q < NR; ++q) dst[q] = sum[q];
+      store_nr<T, NR>(dst, sum);
     }
   }
 }
@@ -694,10 +732,28 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   double s[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) s[r] = 0;
-  for (int p = 0; p < P; ++p) {
-    const T *pp = part + ((size_t)p * nx + K) * NR;
+  // the partials in index order, four quadrant-groups' loads in flight at a time
+  int p = 0;
+  for (; p + 4 <= P; p += 4) {
+    T v[4][NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) s[r] += (double)pp[r];
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[i][r] = 0;
+      add_nr<T, NR>(v[i], part + ((size_t)(p + i) * nx + K) * NR);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) s[r] += (double)v[i][r];
+  }
+  for (; p < P; ++p) {
+    T v[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = 0;
+    add_nr<T, NR>(v, part + ((size_t)p * nx + K) * NR);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) s[r] += (double)v[r];
   }
   const double2 xa = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K);
   const double2 xb = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K + 2);
@@ -752,7 +808,7 @@ static const void *kernel_for_variant(int variant, int apw) {
   }
 }
 
-// coefficient tables are an FP64 feature: the FP32 instances always form the coefficients themselves
+// coefficient tables exist for the FP64 sweeps only
 template <typename T>
 static const void *sweep_kernel_ptr(int variant, int apw, bool tab) {
   if constexpr (sizeof(T) == 8) {
