@@ -201,27 +201,47 @@ void osw_sweep_L00(int n, double h, double ox, double oy, const double *sigt, co
  * b2, using the upwind difference (s_x = -sign(Omega_x)) and spacing h/2 against the zero boundary value.
  * supp (may be NULL): per-cell face bits (1 west, 2 east, 4 south, 8 north) of interior faces across which
  * the reconstruction is suppressed (Section 4, the discontinuous cross-section examples): the difference
- * across such a face is taken as zero. */
-static void recon0(int n, double h, double ox, double oy, const double *u0, const unsigned char *supp, int i,
-                   int j, double sl[2]) {
+ * across such a face is taken as zero.  star (RLMDG*, Section 4.1): from the third cell on the difference is
+ * the centre slope of the quadratic through the cell and its two upwind neighbours, (3u_i - 4u_{i-1} +
+ * u_{i-2}) / (2h); the second cell keeps the two-cell difference. */
+static void recon0(int n, double h, double ox, double oy, const double *u0, const unsigned char *supp, int star,
+                   int i, int j, double sl[2]) {
   int K = j * n + i;
   unsigned m = supp ? supp[K] : 0u;
   double dx, dy;
-  if (ox > 0) dx = i > 0 ? ((m & 1u) ? 0.0 : (u0[K] - u0[K - 1]) / h) : (u0[K] - 0.0) / (h / 2);
-  else dx = i < n - 1 ? ((m & 2u) ? 0.0 : (u0[K + 1] - u0[K]) / h) : (0.0 - u0[K]) / (h / 2);
-  if (oy > 0) dy = j > 0 ? ((m & 4u) ? 0.0 : (u0[K] - u0[K - n]) / h) : (u0[K] - 0.0) / (h / 2);
-  else dy = j < n - 1 ? ((m & 8u) ? 0.0 : (u0[K + n] - u0[K]) / h) : (0.0 - u0[K]) / (h / 2);
+  if (ox > 0) {
+    if (i == 0) dx = (u0[K] - 0.0) / (h / 2);
+    else if (m & 1u) dx = 0.0;
+    else if (star && i >= 2) dx = (3 * u0[K] - 4 * u0[K - 1] + u0[K - 2]) / (2 * h);
+    else dx = (u0[K] - u0[K - 1]) / h;
+  } else {
+    if (i == n - 1) dx = (0.0 - u0[K]) / (h / 2);
+    else if (m & 2u) dx = 0.0;
+    else if (star && i <= n - 3) dx = -(3 * u0[K] - 4 * u0[K + 1] + u0[K + 2]) / (2 * h);
+    else dx = (u0[K + 1] - u0[K]) / h;
+  }
+  if (oy > 0) {
+    if (j == 0) dy = (u0[K] - 0.0) / (h / 2);
+    else if (m & 4u) dy = 0.0;
+    else if (star && j >= 2) dy = (3 * u0[K] - 4 * u0[K - n] + u0[K - 2 * n]) / (2 * h);
+    else dy = (u0[K] - u0[K - n]) / h;
+  } else {
+    if (j == n - 1) dy = (0.0 - u0[K]) / (h / 2);
+    else if (m & 8u) dy = 0.0;
+    else if (star && j <= n - 3) dy = -(3 * u0[K] - 4 * u0[K + n] + u0[K + 2 * n]) / (2 * h);
+    else dy = (u0[K + n] - u0[K]) / h;
+  }
   sl[0] = 0.5 * h * dx;
   sl[1] = 0.5 * h * dy;
 }
 
 /* row 0 of L_l applied to the trial function u0 b0 + R u0 at cell (i, j), given u0 on K and upwind cells */
 static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, double sigt, const double *u0,
-                       const unsigned char *supp, int i, int j) {
+                       const unsigned char *supp, int star, int i, int j) {
   int K = j * n + i;
   double A[4][4], uK[4], sl[2];
   diag_block(e, ox, oy, sigt, A);
-  recon0(n, h, ox, oy, u0, supp, i, j, sl);
+  recon0(n, h, ox, oy, u0, supp, star, i, j, sl);
   uK[0] = u0[K]; uK[1] = sl[0]; uK[2] = sl[1]; uK[3] = 0.0;
   double s = 0.0;
   for (int q = 0; q < 4; ++q) s += A[0][q] * uK[q];
@@ -231,7 +251,7 @@ static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, d
     if (on < 0 && k >= 0) {
       int ki = k % n, kj = k / n;
       double uk[4], sk[2];
-      recon0(n, h, ox, oy, u0, supp, ki, kj, sk);
+      recon0(n, h, ox, oy, u0, supp, star, ki, kj, sk);
       uk[0] = u0[k]; uk[1] = sk[0]; uk[2] = sk[1]; uk[3] = 0.0;
       for (int q = 0; q < 4; ++q) s += on * e->nbrf[f][0][q] * uk[q];
     }
@@ -242,9 +262,10 @@ static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, d
 /* Solve Ltilde00 u0 = b0 for one angle, Ltilde00 = L00 + L01 R (Section 3.3.2): row 0 of L applied to the
  * reconstructed trial function.  The reconstruction at K uses only K and its upwind neighbours, so the
  * system is lower triangular in sweep order; each cell's equation is affine in u0[K] and is solved from two
- * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [n*n]; supp: suppression bits as in recon0, or NULL. */
+ * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [n*n]; supp: suppression bits as in recon0, or NULL; star:
+ * the three-cell reconstruction. */
 void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, const double *b0, double *u0,
-                    const unsigned char *supp) {
+                    const unsigned char *supp, int star) {
   elem_t e;
   build_elem(h, &e);
   memset(u0, 0, sizeof(double) * (size_t)n * n);
@@ -254,9 +275,9 @@ void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, c
       int i = ox > 0 ? ii : n - 1 - ii;
       int K = j * n + i;
       u0[K] = 0.0;
-      double r0 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, i, j);
+      double r0 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, star, i, j);
       u0[K] = 1.0;
-      double r1 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, i, j);
+      double r1 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, star, i, j);
       u0[K] = (b0[K] - r0) / (r1 - r0);
     }
   }

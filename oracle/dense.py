@@ -151,7 +151,7 @@ def _same_material(p):
     return sx, sy
 
 
-def reconstruct(p, u0, alpha, suppress=False):
+def reconstruct(p, u0, alpha, suppress=False, three_cell=False):
     """Upwind reconstruction R_alpha Pi_0 (Section 3.3.1), 2D P1 slopes only.
 
     ``u0``: cell averages ``[n_Omega][n_x]``.  Returns the Legendre coefficients ``[n_Omega][n_x][4]`` of
@@ -160,7 +160,10 @@ def reconstruct(p, u0, alpha, suppress=False):
     taken with alpha at the face midpoint over a spacing h/2 (alpha None means 0).  The face-midpoint value
     of the linear face data (a0 + a1 t) is a0.  ``suppress``: no reconstruction across an interior face where
     the cross sections jump (the remedy Section 4 applies to the kinks at a discontinuity): the upwind
-    difference across such a face is zero.
+    difference across such a face is zero.  ``three_cell`` (RLMDG*, Section 4.1): from the third cell on,
+    delta is the slope at the cell centre of the quadratic with the cell averages of the cell and its two upwind
+    neighbours, (3 u_i - 4 u_{i-1} + u_{i-2}) / (2h); the second cell keeps the two-cell difference and the
+    inflow cell the boundary difference.
     """
     n, h, na = p.n, p.h, p.nang
     out = np.zeros((na, n * n, 4))
@@ -171,18 +174,26 @@ def reconstruct(p, u0, alpha, suppress=False):
         dy = np.zeros((n, n))
         if p.ox[l] > 0:                      # delta^-_x
             dx[:, 1:] = (U[:, 1:] - U[:, :-1]) / h
+            if three_cell:
+                dx[:, 2:] = (3 * U[:, 2:] - 4 * U[:, 1:-1] + U[:, :-2]) / (2 * h)
             aW = alpha[l, 0, :, 0] if alpha is not None else np.zeros(n)
             dx[:, 0] = (U[:, 0] - aW) / (h / 2)
         else:                                # delta^+_x
             dx[:, :-1] = (U[:, 1:] - U[:, :-1]) / h
+            if three_cell:
+                dx[:, :-2] = -(3 * U[:, :-2] - 4 * U[:, 1:-1] + U[:, 2:]) / (2 * h)
             aE = alpha[l, 1, :, 0] if alpha is not None else np.zeros(n)
             dx[:, -1] = (aE - U[:, -1]) / (h / 2)
         if p.oy[l] > 0:
             dy[1:, :] = (U[1:, :] - U[:-1, :]) / h
+            if three_cell:
+                dy[2:, :] = (3 * U[2:, :] - 4 * U[1:-1, :] + U[:-2, :]) / (2 * h)
             aS = alpha[l, 2, :, 0] if alpha is not None else np.zeros(n)
             dy[0, :] = (U[0, :] - aS) / (h / 2)
         else:
             dy[:-1, :] = (U[1:, :] - U[:-1, :]) / h
+            if three_cell:
+                dy[:-2, :] = -(3 * U[:-2, :] - 4 * U[1:-1, :] + U[2:, :]) / (2 * h)
             aN = alpha[l, 3, :, 0] if alpha is not None else np.zeros(n)
             dy[-1, :] = (aN - U[-1, :]) / (h / 2)
         if suppress:
@@ -199,9 +210,9 @@ def reconstruct(p, u0, alpha, suppress=False):
     return out
 
 
-def _Rstar(p, u0, alpha, suppress=False):
+def _Rstar(p, u0, alpha, suppress=False, three_cell=False):
     """R*_alpha applied to the piecewise constants u0: R_alpha Pi_0 u minus its angular average."""
-    R = reconstruct(p, u0, alpha, suppress)
+    R = reconstruct(p, u0, alpha, suppress, three_cell)
     return R - np.einsum("l,lkr->kr", p.w, R)[None]
 
 
@@ -221,7 +232,7 @@ def lm_basis(p):
     return E
 
 
-def rlm_trial_basis(p, suppress=False):
+def rlm_trial_basis(p, suppress=False, three_cell=False):
     """Trial basis of V_h^rlm: xi^{l,p,0} + R*_0 xi^{l,p,0}, then eta^{p,r} (Section 3.3.2)."""
     na, nx = p.nang, p.nx
     E = lm_basis(p)
@@ -230,13 +241,14 @@ def rlm_trial_basis(p, suppress=False):
         for K in range(nx):
             u0 = np.zeros((na, nx))
             u0[l, K] = 1.0
-            Rs = _Rstar(p, u0, None, suppress)
+            Rs = _Rstar(p, u0, None, suppress, three_cell)
             Et[:, l * nx + K] += Rs.ravel()
     return Et
 
 
-def solve(p, variant, suppress=False):
-    """Solve the discrete problem (``suppress``: RLMDG without reconstruction across cross-section jumps).
+def solve(p, variant, suppress=False, three_cell=False):
+    """Solve the discrete problem (``suppress``: RLMDG without reconstruction across cross-section jumps;
+    ``three_cell``: RLMDG* with the three-cell reconstruction).
     Returns a dict with
 
     ``psi``  full coefficients [n_Omega][n_x][4] of the (reconstructed) discrete solution,
@@ -258,8 +270,8 @@ def solve(p, variant, suppress=False):
         out["phi1"] = c[na * nx:].reshape(nx, 3)
     elif variant == "rlm":
         E = lm_basis(p)
-        Et = rlm_trial_basis(p, suppress)
-        rho = _Rstar(p, np.zeros((na, nx)), p.alpha, suppress).ravel()   # affine part R*_alpha 0
+        Et = rlm_trial_basis(p, suppress, three_cell)
+        rho = _Rstar(p, np.zeros((na, nx)), p.alpha, suppress, three_cell).ravel()   # affine part R*_alpha 0
         c = np.linalg.solve(E.T @ B @ Et, E.T @ (Q - B @ rho))
         psi = (Et @ c + rho).reshape(na, nx, 4)
         out["psi0"] = c[:na * nx].reshape(na, nx)

@@ -43,7 +43,7 @@ def _load():
             f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
             f.restype = None
         lib.osw_sweep_Lt00.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
-                                       ctypes.POINTER(ctypes.c_ubyte)]
+                                       ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int]
         lib.osw_sweep_Lt00.restype = None
         lib.osw_elem_tables.argtypes = [ctypes.c_double, dp]
         lib.osw_elem_tables.restype = None
@@ -66,9 +66,12 @@ class SweepOracle:
     """Matrix-free block operators of one problem.  ``threads`` angles are processed concurrently; every
     angular sum is accumulated in angle order, so results do not depend on the thread count."""
 
-    def __init__(self, p, threads=None, literal_b11=False, suppress=False):
+    def __init__(self, p, threads=None, literal_b11=False, suppress=False, three_cell=False):
+        """``suppress``: RLMDG without reconstruction across cross-section jumps; ``three_cell``: RLMDG* (the
+        three-cell upwind reconstruction from the third cell on)."""
         self.p = p
         self.literal_b11 = literal_b11
+        self.three_cell = three_cell
         self.n, self.h, self.nx, self.na = p.n, p.h, p.nx, p.nang
         self.suppress = suppress
         self.supp = self._suppression_bits() if suppress else None
@@ -100,6 +103,7 @@ class SweepOracle:
         args = [self.n, self.h, float(self.p.ox[l]), float(self.p.oy[l]), _ptr(self.sigt), _ptr(a), _ptr(out)]
         if name == "osw_sweep_Lt00":
             args.append(None if self.supp is None else self.supp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+            args.append(1 if self.three_cell else 0)
         getattr(self.lib, name)(*args)
         return out
 
@@ -291,18 +295,26 @@ class SweepOracle:
             left = np.concatenate([bw[:, None], U[:, :-1]], axis=1)
             sp = np.concatenate([np.full((n, 1), h / 2), np.full((n, n - 1), h)], axis=1)
             dx = (U - left) / sp
+            if self.three_cell and n > 2:      # RLMDG*: quadratic through three upwind cell averages
+                dx[:, 2:] = (3 * U[:, 2:] - 4 * U[:, 1:-1] + U[:, :-2]) / (2 * h)
         else:
             right = np.concatenate([U[:, 1:], be[:, None]], axis=1)
             sp = np.concatenate([np.full((n, n - 1), h), np.full((n, 1), h / 2)], axis=1)
             dx = (right - U) / sp
+            if self.three_cell and n > 2:
+                dx[:, :-2] = (-3 * U[:, :-2] + 4 * U[:, 1:-1] - U[:, 2:]) / (2 * h)
         if p.oy[l] > 0:
             down = np.concatenate([bs[None, :], U[:-1, :]], axis=0)
             sp = np.concatenate([np.full((1, n), h / 2), np.full((n - 1, n), h)], axis=0)
             dy = (U - down) / sp
+            if self.three_cell and n > 2:
+                dy[2:, :] = (3 * U[2:, :] - 4 * U[1:-1, :] + U[:-2, :]) / (2 * h)
         else:
             up = np.concatenate([U[1:, :], bn[None, :]], axis=0)
             sp = np.concatenate([np.full((n - 1, n), h), np.full((1, n), h / 2)], axis=0)
             dy = (up - U) / sp
+            if self.three_cell and n > 2:
+                dy[:-2, :] = (-3 * U[:-2, :] + 4 * U[1:-1, :] - U[2:, :]) / (2 * h)
         if self.supp is not None:
             m = self.supp.reshape(n, n)
             dx = np.where(m & (1 if p.ox[l] > 0 else 2), 0.0, dx)
