@@ -216,6 +216,16 @@ def _Rstar(p, u0, alpha, suppress=False, three_cell=False):
     return R - np.einsum("l,lkr->kr", p.w, R)[None]
 
 
+def p0_basis(p):
+    """Basis matrix of V_{h,0} (Section 3.1): the per-direction cell constants xi^{l,p,0}."""
+    na, nx = p.nang, p.nx
+    E = np.zeros((na * nx * 4, na * nx))
+    for l in range(na):
+        for K in range(nx):
+            E[(l * nx + K) * 4, l * nx + K] = 1.0
+    return E
+
+
 def lm_basis(p):
     """Basis matrix of V_h^lm: columns xi^{l,p,0} (l, p) then eta^{p,r} = sum_l xi^{l,p,r} (p, r = 1..3)."""
     na, nx = p.nang, p.nx
@@ -262,6 +272,11 @@ def solve(p, variant, suppress=False, three_cell=False):
     out = {}
     if variant == "std":
         psi = np.linalg.solve(B, Q).reshape(na, nx, 4)
+    elif variant == "p0":
+        E = p0_basis(p)
+        c = np.linalg.solve(E.T @ B @ E, E.T @ Q)
+        psi = (E @ c).reshape(na, nx, 4)
+        out["psi0"] = c.reshape(na, nx)
     elif variant == "lm":
         E = lm_basis(p)
         c = np.linalg.solve(E.T @ B @ E, E.T @ Q)

@@ -11,7 +11,8 @@ inverses come from ``csweep.c``.
   recovery Psi = L^-1 (M Phi + Q) (eq-sndg-final-sweep).
 * LMDG (Section 3.2): B11 = Sigma L11 Sigma^T - Sigma M1 (eq-lmdg-psi1), K applied as eq-nonrec-block,
   right-hand side of eq-lmdg-reducemat, recovery eq-lm-step4.
-* RLMDG (Section 3.3.2), with the readings listed in DESIGN.md: the tilde blocks and Q-tilde as printed;
+* RLMDG (Section 3.3.2), read as follows where the printed system is inconsistent: the tilde blocks and
+  Q-tilde as printed;
   with X1 = (B11^-1 Sigma Ltilde10 + P1 R) Psi0 the second block row of the reduced operator and of the
   right-hand side is G' = Sigma Ltilde10 + B11 P1 R (= B11 times the printed row's operator), which is what
   applying Sigma Ltilde10 to eq-rlmdg-psi0 and closing with X1 produces; recovery Psi0 = Ltilde00^-1
@@ -405,12 +406,32 @@ class SweepOracle:
         out[:, :, 1:3] += RR
         return out
 
+    # ---------------------------------------------------------------- P0-DG (V_{h,0}, Section 3.1)
+    def K_p0(self, X):
+        """Piecewise-constant S_N-DG reduced to the cell-average scalar flux: X0 - P0 L00^-1 M0 X0 (the
+        scheme of Section 2.1.1 on V_{h,0}); the slope entries of the 4-vector are carried by the identity."""
+        X = X.reshape(self.nx, 4)
+        Psi0 = np.stack(self._angles_map(lambda l: self.L00inv(l, self.M0(l, X[:, 0]))))
+        out = X.copy()
+        out[:, 0] = X[:, 0] - self.P0(Psi0)
+        return out
+
+    def rhs_p0(self):
+        F = np.stack(self._angles_map(lambda l: self.L00inv(l, self.Q(l)[:, 0])))
+        out = np.zeros((self.nx, 4))
+        out[:, 0] = self.P0(F)
+        return out
+
+    def recover_p0(self, X):
+        X0 = X.reshape(self.nx, 4)[:, 0]
+        return np.stack(self._angles_map(lambda l: self.L00inv(l, self.M0(l, X0) + self.Q(l)[:, 0])))
+
     # ---------------------------------------------------------------- drivers
     def K(self, variant, X):
-        return {"std": self.K_std, "lm": self.K_lm, "rlm": self.K_rlm}[variant](X)
+        return {"std": self.K_std, "lm": self.K_lm, "rlm": self.K_rlm, "p0": self.K_p0}[variant](X)
 
     def rhs(self, variant):
-        return {"std": self.rhs_std, "lm": self.rhs_lm, "rlm": self.rhs_rlm}[variant]()
+        return {"std": self.rhs_std, "lm": self.rhs_lm, "rlm": self.rhs_rlm, "p0": self.rhs_p0}[variant]()
 
     def dense_K(self, variant):
         """The reduced operator as a dense matrix (column j = K e_j); small meshes only."""
@@ -429,7 +450,7 @@ class SweepOracle:
         ``precond='jacobi'`` (default for the low-memory variants) right-preconditions GMRES by
         diag(I, diag(B11))^-1, which leaves the residual of the original system unchanged."""
         if precond is None:
-            precond = "none" if variant == "std" else "jacobi"
+            precond = "none" if variant in ("std", "p0") else "jacobi"
         b = self.rhs(variant).ravel()
         n4 = b.size
         if direct is None:
@@ -457,6 +478,11 @@ class SweepOracle:
         out = {"X": X, **info}
         if variant == "std":
             psi = self.recover_std(X)
+        elif variant == "p0":
+            Psi0 = self.recover_p0(X)
+            psi = np.zeros((self.na, self.nx, 4))
+            psi[:, :, 0] = Psi0
+            out.update(psi0=Psi0)
         elif variant == "lm":
             Psi0, Phi1 = self.recover_lm(X)
             psi = np.zeros((self.na, self.nx, 4))
