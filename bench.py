@@ -15,6 +15,7 @@ time to 1e-8 for the mixed and the FP64 solver is reported beside it.
 import argparse
 import json
 import os
+import tempfile
 import subprocess
 import sys
 import threading
@@ -64,7 +65,8 @@ class ClockSampler:
     def __init__(self, idx):
         self.idx = idx
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{idx}.csv")
+        out = os.environ.get("LMDG_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out, f"clocks_rank{idx}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -341,7 +343,7 @@ def run_gpu(args, rank, ws, dist):
 
 
 def run_profile(args):
-    """Small case for ncu: 512x512 cells, S16, the bench media; per round the three FP32 non-storing sweeps (as
+    """Small case for ncu: 512x512 cells, S16, the bench media; per pass the three FP32 non-storing sweeps (as
     inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2) and the three
     FP64 source sweeps (as in the refinement residual); two rounds (sweep kernels 1-7 untimed, 8-14 for the
     capture)."""

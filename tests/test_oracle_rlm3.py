@@ -11,6 +11,9 @@ boundary difference in the inflow cell).
   reproduces them exactly.
 * The paper reports RLMDG* second-order accurate with an error well below RLMDG's: measured here on the
   fabricated solution sin(x + y), order near 2 from 8 to 16 cells and an error at least twice smaller.
+* A limitation of the reading in 2D (the paper tests RLMDG* in 1D only): in optically thin cells the sweep
+  recurrence of the three-cell reconstruction amplifies along a ray -- the response to a point source grows
+  much faster than linearly with the number of cells, where RLMDG's grows linearly.
 """
 import numpy as np
 import pytest
@@ -71,3 +74,18 @@ def test_second_order_and_below_rlmdg():
     order = np.log2(err[(8, True)] / err[(16, True)])
     assert 1.8 < order < 2.6, order
     assert err[(16, False)] > 2 * err[(16, True)]
+
+
+def test_thin_cells_amplify():
+    from workloads.problems import uniform_problem
+    peak = {}
+    for n in (64, 256):
+        p = uniform_problem(n, 8, 1e-3 * n, 0.0, 1.0)          # sigma_t h = 1e-3
+        for star in (False, True):
+            so = SweepOracle(p, three_cell=star)
+            b = np.zeros(p.nx)
+            b[0] = 1.0
+            peak[(n, star)] = max(np.abs(so.Lt00inv(l, b * p.w[l])).max()
+                                  for l in np.where((p.ox > 0) & (p.oy > 0))[0])
+    assert 3.5 < peak[(256, False)] / peak[(64, False)] < 4.5       # RLMDG: linear in n (the h scaling)
+    assert peak[(256, True)] / peak[(64, True)] > 50
