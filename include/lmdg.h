@@ -33,8 +33,10 @@ typedef struct lmdg_ctx lmdg_ctx;
 
 /* Scheme: standard S_N-DG with the full Q1 space V_h (eq-sndg-scheme); low-memory LMDG with
  * V_h^lm = V_{h,0} + D_{h,1} (eq-gene-scheme, Section 3.2); reconstructed RLMDG (eq-rlmdg-vari,
- * Section 3.3). */
-enum { LMDG_STD = 0, LMDG_LM = 1, LMDG_RLM = 2 };
+ * Section 3.3); P0-DG, the S_N-DG scheme on the piecewise constants V_{h,0} (the comparison scheme of
+ * Section 3.1: first order, without the diffusion limit).  For P0-DG the reduced vector keeps the [n*n][4]
+ * layout; its unknown is the cell average (entry 0) and entries 1..3 are carried by the identity. */
+enum { LMDG_STD = 0, LMDG_LM = 1, LMDG_RLM = 2, LMDG_P0 = 3 };
 
 /* Arithmetic of the sweeps inside lmdg_solve.  FP64: everything in double.  FP32: sweeps in float inside an
  * FP64 iterative-refinement loop (residuals, GMRES orthogonalisation and least squares stay FP64).
@@ -90,6 +92,12 @@ typedef struct {
   int suppress;        /* LMDG_RLM only, 1: no reconstruction across an interior face where sigma_s or sigma_a
                           changes (the remedy of Section 4 for the kinks at a cross-section discontinuity: the
                           upwind difference across such a face is zero); default 0 */
+  int recon;           /* LMDG_RLM only, 1: RLMDG* -- from the third cell on, the reconstructed slope is the centre
+                          slope of the quadratic through the cell averages of the cell and its two upwind
+                          neighbours, (3 u_i - 4 u_{i-1} + u_{i-2}) / (2h) (the three-cell reconstruction of
+                          Section 4.1); not combined with suppress; default 0 (two-cell, Section 3.3.1).  Its
+                          sweep amplifies along rays through optically thin cells (sigma_t h below about 0.01 over
+                          hundreds of cells), where round-off then dominates */
 } lmdg_options;
 
 typedef struct {

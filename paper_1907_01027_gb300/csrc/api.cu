@@ -122,11 +122,11 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     c->ytr_prec = want;
   }
   CK(cudaEventRecord(c->ev0, s));
-  CK(launch_sweep<T>(c->variant, a, s));
+  CK(launch_sweep<T>(c->kvar, a, s));
   CK(cudaEventRecord(c->ev1, s));
   c->ev_pending = f64 ? 0 : 1;
   // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
-  CK(launch_epilogue<T>(c->variant, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
+  CK(launch_epilogue<T>(c->kvar, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
                         c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
   if (f64) c->sweeps64++; else c->sweeps32++;
   return 0;
@@ -147,11 +147,12 @@ int check_error_word(lmdg_ctx *c, cudaStream_t s) {
 }
 
 // phi = scalar-flux moments from the partial reductions of the last sweep at X (low-memory variants):
-// phi0 = P0 psi0, phi_r = -W_r + (P1 R psi0)_r (RLMDG, alpha part removed), W = X1 - z the GMRES unknown.
+// phi0 = P0 psi0, phi_r = -W_r + (P1 R psi0)_r (RLMDG, alpha part removed), W = X1 - z the GMRES unknown;
+// P0-DG: phi0 only (no slopes).
 template <typename T, int VAR>
 __global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const double *__restrict__ X,
                            const double *__restrict__ p1ra, double *__restrict__ phi) {
-  constexpr int NR = (VAR == 2) ? 6 : 4;
+  constexpr int NR = VAR == kP0 ? 2 : ((VAR == 2) ? 6 : 4);
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   double s[NR];
@@ -161,6 +162,7 @@ __global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const doub
   const double *x = X + 4 * (size_t)K;
   double *o = phi + 4 * (size_t)K;
   o[0] = s[0];
+  if (VAR == kP0) { o[1] = 0; o[2] = 0; o[3] = 0; return; }
   o[1] = -x[1]; o[2] = -x[2]; o[3] = -x[3];
   if (VAR == 2) {
     o[1] += s[4] - (p1ra ? p1ra[2 * (size_t)K] : 0.0);
@@ -213,7 +215,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   double *hdev = c->red + mdot_partial_len(c->red_len);          // [m+2]
   double *h2dev = hdev + (m + 2);
   double *ydev = h2dev + (m + 2);
-  const int pmode = (c->variant != LMDG_STD && c->opt.precond) ? 1 : 0;
+  const int pmode = ((c->variant == LMDG_LM || c->variant == LMDG_RLM) && c->opt.precond) ? 1 : 0;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
   g[0] = rnorm;
   CK(axpby(V, 1.0 / rnorm, r, 0.0, N, s));
@@ -288,6 +290,7 @@ int lmdg_default_options(lmdg_options *o) {
   o->spin_limit = 1LL << 26;
   o->device = 0;
   o->suppress = 0;
+  o->recon = 0;
   return 0;
 }
 
@@ -346,7 +349,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   const int n = mesh->n;
   if (n < 1 || n > 65536 || !(mesh->h > 0) || !std::isfinite(mesh->h)) return LMDG_ERR_ARG;
   if (!(eps > 1e-12) || !std::isfinite(eps)) return LMDG_ERR_ARG;
-  if (variant < LMDG_STD || variant > LMDG_RLM || q_layout < 0 || q_layout > 2) return LMDG_ERR_ARG;
+  if (variant < LMDG_STD || variant > LMDG_P0 || q_layout < 0 || q_layout > 2) return LMDG_ERR_ARG;
   const int na = quad->n;
   if (na < 4 || na > 1024 || na % 4 || !quad->ox || !quad->oy || !quad->w) return LMDG_ERR_QUAD;
   double wsum = 0;
@@ -370,7 +373,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   lmdg_default_options(&o);
   if (opt) o = *opt;
   if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
-      (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM))
+      (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || (o.recon != 0 && o.recon != 1) ||
+      (o.recon && (variant != LMDG_RLM || o.suppress)))
     return LMDG_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
@@ -379,6 +383,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   lmdg_ctx *c = new (std::nothrow) lmdg_ctx();
   if (!c) return LMDG_ERR_NOMEM;
   c->n = n; c->nx = (int)nx; c->nang = na; c->nq = na / 4; c->variant = variant; c->q_layout = q_layout;
+  c->kvar = variant == LMDG_P0 ? kP0 : ((variant == LMDG_RLM && o.recon) ? kRlmStar : variant);
   c->has_alpha = alpha != nullptr; c->dev = o.device; c->h = mesh->h; c->eps = eps;
   c->x0 = mesh->x0; c->y0 = mesh->y0; c->opt = o;
   auto fail = [&](int e) { lmdg_destroy(c); return e; };
@@ -513,8 +518,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       }
     if ((e = upload(&c->supp, bits))) return fail(e);
   }
-  c->g64 = choose_geom(variant, n, c->nq, true);
-  c->g32 = choose_geom(variant, n, c->nq, false);
+  c->g64 = choose_geom(c->kvar, n, c->nq, true);
+  c->g32 = choose_geom(c->kvar, n, c->nq, false);
   if (c->g64.units() == 0 || c->g32.units() == 0) return fail(LMDG_ERR_CUDA);
   if (std::getenv("LMDG_VERBOSE"))
     std::fprintf(stderr, "lmdg: n=%d n_omega=%d variant=%d fp64 shape groups=%d warps=%d apw=%d | fp32 groups=%d "
@@ -523,8 +528,9 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   const size_t pe = std::max(part_elems(c->g64, c->nx), part_elems(c->g32, c->nx));
   if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   const int strips = (n + 31) / 32;
-  if (cudaMalloc(&c->ytr, sizeof(double) * (size_t)na * strips * n * 3) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
-  c->ytr_words = 2 * (size_t)na * strips * n * 3;
+  const size_t ytr_elems = (size_t)na * strips * n * kTraceStride;
+  if (cudaMalloc(&c->ytr, sizeof(double) * ytr_elems) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  c->ytr_words = 2 * ytr_elems;
   c->ytr_dirty = true;
   if (cudaMalloc(&c->cellsrc, sizeof(double) * 4 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMalloc(&c->cellsh, sizeof(double) * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
@@ -554,7 +560,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     }
     c->nmat = (int)uniq.size();
     c->ncls = (int)(cab.size() / 2);
-    c->ncoef = coef_count(variant);
+    c->ncoef = coef_count(c->kvar);
     const size_t tbytes = sizeof(double) * (size_t)c->nmat * c->ncls * c->ncoef;
     double *cabd = nullptr;
     bool ok = cudaMalloc(&c->coef, tbytes) == cudaSuccess && cudaMalloc(&c->mat, sizeof(int) * nx) == cudaSuccess &&
@@ -565,7 +571,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
          cudaMemcpy(c->cls, clsv.data(), sizeof(int) * na, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(c->matsh, uniq.data(), sizeof(double) * c->nmat, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(cabd, cab.data(), sizeof(double) * cab.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         build_coef_tables(variant, c->nmat, c->ncls, c->matsh, cabd, c->coef, 0) == cudaSuccess &&
+         build_coef_tables(c->kvar, c->nmat, c->ncls, c->matsh, cabd, c->coef, 0) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
     cudaFree(cabd);
     if (!ok) {   // no tables: the FP64 sweeps compute the coefficients themselves
@@ -692,6 +698,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
       const double *part = reinterpret_cast<const double *>(c->part);
       add_launches(1);
       if (c->variant == LMDG_LM) phi_kernel<double, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
+      else if (c->variant == LMDG_P0) phi_kernel<double, kP0><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, nullptr, P);
       else phi_kernel<double, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
       CK(cudaGetLastError());
     }
@@ -787,7 +794,7 @@ int lmdg_b11_solve(lmdg_ctx *c, const double *r, double *z, double tol, int *ite
 int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double *dq, double *J, lmdg_stats *st,
                  int flags, void *stream) {
   if (!c || !g) return LMDG_ERR_ARG;
-  if (c->variant == LMDG_RLM || c->q_layout == 2) return LMDG_ERR_ARG;
+  if (c->variant == LMDG_RLM || c->variant == LMDG_P0 || c->q_layout == 2) return LMDG_ERR_ARG;
   if (!c->rev_ok) return LMDG_ERR_QUAD;
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;

@@ -33,6 +33,9 @@ constexpr int kMaxA = 4;        // cap on directions per warp (template instance
 #endif
 constexpr int kChunk = LMDG_CHUNK;   // steps per chunk: cell staging, inflow staging, one CTA barrier
 constexpr unsigned kTraceEmpty = 0xFFF7FFF7u;   // 32-bit pattern of a strip trace not yet written (a NaN)
+constexpr int kTraceStride = 4;      // trace values stored per (direction, strip boundary, column)
+constexpr int kRlmStar = 3;          // kernel variant of RLMDG* (LMDG_RLM with the three-cell reconstruction)
+constexpr int kP0 = 4;               // kernel variant of P0-DG (LMDG_P0)
 
 // Arguments of one sweep launch (everything a kernel reads or writes).
 template <typename T>
@@ -49,7 +52,7 @@ struct SweepArgs {
   void *psi;           // storing sweep output or null (sorted->user order through perm)
   int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
   const int *perm;     // [nang] sorted index -> user index
-  T *ytr;              // [nang][strips][n][3] traces crossing strip boundaries, kTraceEmpty when unwritten
+  T *ytr;              // [nang][strips][n][kTraceStride] strip-boundary traces, kTraceEmpty when unwritten
   unsigned *ctrl;      // [0] ticket, [1] error
   long long spin_limit;
   const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
@@ -101,6 +104,7 @@ cudaError_t quad_moments(int nang, const double *ox, const double *oy, const dou
 // Context
 struct lmdg_ctx {
   int n = 0, nx = 0, nang = 0, nq = 0, variant = 0, q_layout = 0, has_alpha = 0, dev = 0;
+  int kvar = 0;                            // kernel variant: the scheme, kRlmStar for RLMDG*, kP0 for P0-DG
   double h = 0, eps = 0, x0 = 0, y0 = 0;
   lmdg_options opt{};
   int *perm = nullptr;                     // device [nang]

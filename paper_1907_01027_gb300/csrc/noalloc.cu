@@ -96,7 +96,7 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   const size_t off_cellh = off_cell + align256(sizeof(double) * 4 * nx);
   const size_t off_part = off_cellh + align256(sizeof(double) * nx);
   const size_t off_ytr = off_part + align256(sizeof(double) * 4 * g.groups * nx * NR);
-  const size_t need = off_ytr + sizeof(double) * (size_t)n_omega * g.strips * n * 3;
+  const size_t need = off_ytr + sizeof(double) * (size_t)n_omega * g.strips * n * kTraceStride;
   if (need > kScratchBytes) return LMDG_ERR_ARG;   // problem too large for the fixed scratch
   unsigned char *base = nullptr;
   if (int e = scratch_for_current_device(&base, s)) return e;
@@ -125,7 +125,7 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   a.spin_limit = spin_limit;
   // strip traces start empty (the buffer is shared with earlier calls of any size)
   if (fill_u32(reinterpret_cast<unsigned *>(base + off_ytr), kTraceEmpty,
-               2 * (size_t)n_omega * g.strips * n * 3, s) != cudaSuccess)
+               2 * (size_t)n_omega * g.strips * n * kTraceStride, s) != cudaSuccess)
     return LMDG_ERR_CUDA;
   double *qm = reinterpret_cast<double *>(base + off_qm);
   if (quad_moments(n_omega, ox, oy, w, qm, s) != cudaSuccess) return LMDG_ERR_CUDA;

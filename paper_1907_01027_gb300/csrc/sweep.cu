@@ -180,7 +180,8 @@ __device__ __forceinline__ int mat_of(float v) { return __float_as_int(v); }
 // [2][kChunk][32], upstream traces [W][APW][kChunk][NS], RLMDG suppression bits [2][kChunk][32].
 template <typename T>
 size_t sweep_smem_bytes(int variant, int warps, int apw) {
-  const int NR = variant == LMDG_RLM ? 6 : 4, NS = variant == LMDG_RLM ? 3 : 2;
+  const int NR = variant == kP0 ? 2 : (variant >= LMDG_RLM ? 6 : 4);
+  const int NS = variant == kP0 ? 1 : (variant == kRlmStar ? 4 : (variant == LMDG_RLM ? 3 : 2));
   return sizeof(T) * ((size_t)2 * kChunk * warps * NR * 32 + (size_t)2 * kChunk * 32 * 5 +
                       (size_t)warps * apw * kChunk * NS) +
          sizeof(unsigned) * (size_t)2 * kChunk * 32;
@@ -210,9 +211,12 @@ __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, co
     o[1] = (2 * h / 3) * (s * (T)Xa.y + eps * q4[1]);
     o[2] = (2 * h / 3) * (s * (T)Xb.x + eps * q4[2]);
     o[3] = (2 * h / 9) * (s * (T)Xb.y + eps * q4[3]);
+  } else if (VAR == kP0) {
+    o[0] = 2 * h * (s * (T)Xa.x + eps * q4[0]);
+    o[1] = 0; o[2] = 0; o[3] = 0;
   } else {
     T p1 = 0, p2 = 0;
-    if (VAR == 2 && source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; }
+    if (VAR >= 2 && source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; }
     o[0] = 2 * h * (s * (T)Xa.x + eps * q4[0]);
     o[1] = -((T)Xa.y + p1);
     o[2] = -((T)Xb.x + p2);
@@ -230,8 +234,10 @@ __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, co
 //             system (a00 a03; a03 a33) of the (u0, u3) unknowns, c0 = a33/det, c1 = a03/det, c3 = a00/det;
 //   LMDG: 1/d0;
 //   RLMDG: 1/(d0 + cx + cy) with cx = a for a reconstructed x slope, 2a on an inflow x face, 0 where the
-//          reconstruction is suppressed (likewise cy), at index (x state) + 3 (y state), states in that order.
-int coef_count(int variant) { return variant == LMDG_STD ? 9 : (variant == LMDG_LM ? 1 : 9); }
+//          reconstruction is suppressed (likewise cy), at index (x state) + 3 (y state), states in that order;
+//   RLMDG*: the same with cx = 3a/2 for the three-cell slope, 2a on an inflow face, a in the second cell;
+//   P0-DG: 1/d0 as LMDG.
+int coef_count(int variant) { return (variant == LMDG_LM || variant == kP0) ? 1 : 9; }
 
 __global__ void coef_kernel(int variant, int nmat, int ncls, const double *__restrict__ matsh,
                             const double *__restrict__ cls_ab, double *__restrict__ coef) {
@@ -250,11 +256,13 @@ __global__ void coef_kernel(int variant, int nmat, int ncls, const double *__res
     const double det = a00 * a33 - a03 * a03;
     o[0] = i1; o[1] = i2; o[2] = 2 * a * i1; o[3] = 2 * b * i2; o[4] = c23 * b * i1; o[5] = c23 * a * i2;
     o[6] = a33 / det; o[7] = a03 / det; o[8] = a00 / det;
-  } else if (variant == LMDG_LM) {
+  } else if (variant == LMDG_LM || variant == kP0) {
     coef[id] = 1.0 / d0;
   } else {
     double *o = coef + (size_t)id * 9;
-    const double cx[3] = {a, 2 * a, 0.0}, cy[3] = {b, 2 * b, 0.0};
+    const bool star = variant == kRlmStar;
+    const double cx[3] = {star ? 1.5 * a : a, 2 * a, star ? a : 0.0};
+    const double cy[3] = {star ? 1.5 * b : b, 2 * b, star ? b : 0.0};
     for (int ys = 0; ys < 3; ++ys)
       for (int xs = 0; xs < 3; ++xs) o[xs + 3 * ys] = 1.0 / (d0 + cx[xs] + cy[ys]);
   }
@@ -277,9 +285,10 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 // instances only), else they are formed in the kernel from sigma_t h.
 template <typename T, int VAR, int APW, bool TAB>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
-  constexpr int NR = (VAR == 2) ? 6 : 4;   // reduced values per cell
-  constexpr int NS = (VAR == 2) ? 3 : 2;   // trace values passed downwind per face
-  constexpr int NC = VAR == 0 ? 9 : (VAR == 1 ? 1 : 9);   // table coefficients per (material, class)
+  constexpr bool P0 = VAR == kP0;         // P0-DG: the LMDG row-0 solve without slopes
+  constexpr int NR = P0 ? 2 : ((VAR >= 2) ? 6 : 4);   // reduced values per cell
+  constexpr int NS = P0 ? 1 : (VAR == 3 ? 4 : (VAR == 2 ? 3 : 2));   // trace values passed downwind per face
+  constexpr int NC = (VAR == 1 || P0) ? 1 : 9;   // table coefficients per (material, class)
   constexpr int C = kChunk;
   // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
   constexpr bool kF64 = sizeof(T) == 8;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       Wx[k] = flip(2 * w * a, mx); Wy[k] = flip(2 * w * b, my);
       if (idx < gcount) { Ga += w * c23 * a; Gb += w * c23 * b; }
     }
-    if (VAR == 2) {
+    if (VAR >= 2 && !P0) {
       Dx[k] = flip(w * (2 * a + c23 * b), mx); Dy[k] = flip(w * (2 * b + c23 * a), my);
       nWxb[k] = flip(w * c23 * b, mx ^ 0x80000000u); nWya[k] = flip(w * c23 * a, my ^ 0x80000000u);
       W3a[k] = flip(w * c23 * a, mxy); W3b[k] = flip(w * c23 * b, mxy);
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     const int x = t0 + s;
     if (k >= nA || x >= n) return nullptr;
     const int ak = quad * A.nq + g0 + min(warp + k * W, gcount - 1);
-    return A.ytr + (((size_t)ak * A.g.strips + (strip - 1)) * n + x) * 3 + c;
+    return A.ytr + (((size_t)ak * A.g.strips + (strip - 1)) * n + x) * kTraceStride + c;
   };
   T pre[NI];
 #pragma unroll
@@ -480,6 +489,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
           ysup = (mk & (sy > 0 ? 4u : 8u)) != 0;
         }
         const T *cf = TAB ? tab + (size_t)mat_of(st) * tab_stride : nullptr;
+        // RLMDG*: the reconstruction of this cell in x (and y) -- inflow cell, second cell (two-cell
+        // difference) or interior (three-cell): slope = f0 u0 - f1 u_up + f2 u_upup, row-0 rhs gains
+        // a (g1 u_up - g2 u_upup), table state 1 / 2 / 0
+        T f0x = 0, f1x = 0, f2x = 0, g1x = 0, g2x = 0, f0y = 0, f1y = 0, f2y = 0, g1y = 0, g2y = 0, cdx = 0, cdy = 0;
+        int stx = 0, sty = 0;
+        if (VAR == 3) {
+          if (xbnd) { stx = 1; f0x = 1; cdx = 2; }
+          else if (x == 1) { stx = 2; f0x = (T)0.5; f1x = (T)0.5; g1x = 1; cdx = 1; }
+          else { f0x = (T)0.75; f1x = 1; f2x = (T)0.25; g1x = 2; g2x = (T)0.5; cdx = (T)1.5; }
+          if (ybnd) { sty = 1; f0y = 1; cdy = 2; }
+          else if (row == 1) { sty = 2; f0y = (T)0.5; f1y = (T)0.5; g1y = 1; cdy = 1; }
+          else { f0y = (T)0.75; f1y = 1; f2y = (T)0.25; g1y = 2; g2y = (T)0.5; cdy = (T)1.5; }
+        }
 
         T acc[NR];
 #pragma unroll
@@ -497,7 +519,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         for (int k = 0; k < APW; ++k) {
           if (k < nA) {
             // inflow from the cell below (LMDG: the mean trace only; its slope trace is per lane)
-            constexpr int NSH = VAR == 1 ? 1 : NS;
+            constexpr int NSH = (VAR == 1 || P0) ? 1 : NS;
             T yin[NS];
 #pragma unroll
             for (int c = 0; c < NSH; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
@@ -527,7 +549,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
                 S += 2 * h * A.eps * qp[0];
               }
-              if (VAR == 0) {
+              if constexpr (VAR == 0) {
                 // ---------------- standard Q1 block solve; inflow traces vanish outside the mesh
                 T sa1 = A1, sa2 = A2, sa3 = A3;
                 if (qp) {
@@ -592,7 +614,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   T *pp = reinterpret_cast<T *>(A.psi) + ((size_t)uA[k] * nx + K) * 4;
                   pp[0] = u0; pp[1] = flip(u1, mx); pp[2] = flip(u2, my); pp[3] = flip(u3, mxy);
                 }
-              } else if (VAR == 1) {
+              } else if constexpr (VAR == 1 || P0) {
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
                 //   rhs = S + 2a (U0 - A1) + 2b (V0 - A2), U0 / V0 the mean inflow traces (alpha on the boundary)
                 const T U0 = xs[k][0], V0 = yin[0];
@@ -605,29 +627,49 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
                 } else {
                   acc[0] = fma(wl, u0, acc[0]);
-                  acc[1] = fma(Wx[k], U0 - u0, acc[1]);
-                  acc[2] = fma(Wy[k], V0 - u0, acc[2]);
+                  if constexpr (!P0) {
+                    acc[1] = fma(Wx[k], U0 - u0, acc[1]);
+                    acc[2] = fma(Wy[k], V0 - u0, acc[2]);
+                  }
                 }
-                xs[k][0] = u0 + A1;
-                ys[k][0] = u0 + A2;
-                ys[k][1] = A13;
+                if constexpr (P0) {
+                  xs[k][0] = u0;
+                  ys[k][0] = u0;
+                } else {
+                  xs[k][0] = u0 + A1;
+                  ys[k][0] = u0 + A2;
+                  ys[k][1] = A13;
+                }
                 if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
               } else {
                 // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
                 //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
-                //   a suppressed face; 2a (h/2) delta_x enters row 0 through L01
+                //   a suppressed face; 2a (h/2) delta_x enters row 0 through L01.  RLMDG*: the three-cell slope
+                //   (3 u0 - 4 u0_up + u0_upup)/4 from the third cell on
                 const T U0 = xs[k][0], U1 = xs[k][1], Ux = xs[k][2];
                 const T V0 = yin[0], V1 = yin[1], Vy = yin[2];
                 T rhs = c2a[k] * (U0 - A1) + (c2b[k] * (V0 - A2) + S);
-                rhs += a * (xsup ? (T)0 : Ux) + bb * (ysup ? (T)0 : Vy);
-                if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
-                const int bi = (xbnd ? 1 : (xsup ? 2 : 0)) + 3 * (ybnd ? 1 : (ysup ? 2 : 0));
-                const T inv = TAB ? (T)__ldg(cf + kA[k] + bi)
-                                  : rcp(2 * st + a * (T)(xbnd ? 4 : (xsup ? 2 : 3)) +
-                                        bb * (T)(ybnd ? 4 : (ysup ? 2 : 3)));
-                const T u0 = rhs * inv;
-                T rec1 = (xbnd ? (T)1 : (xsup ? (T)0 : (T)0.5)) * (u0 - Ux);
-                T rec2 = (ybnd ? (T)1 : (ysup ? (T)0 : (T)0.5)) * (u0 - Vy);
+                T u0, rec1, rec2;
+                if constexpr (VAR == 3) {
+                  const T Uxx = xs[k][3], Vyy = yin[3];
+                  rhs = fma(a, g1x * Ux - g2x * Uxx, fma(bb, g1y * Vy - g2y * Vyy, rhs));
+                  if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
+                  const T inv = TAB ? (T)__ldg(cf + kA[k] + stx + 3 * sty)
+                                    : rcp(2 * st + a * (2 + cdx) + bb * (2 + cdy));
+                  u0 = rhs * inv;
+                  rec1 = f0x * u0 - (f1x * Ux - f2x * Uxx);
+                  rec2 = f0y * u0 - (f1y * Vy - f2y * Vyy);
+                } else {
+                  rhs = fma(a, xsup ? (T)0 : Ux, fma(bb, ysup ? (T)0 : Vy, rhs));
+                  if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
+                  const int bi = (xbnd ? 1 : (xsup ? 2 : 0)) + 3 * (ybnd ? 1 : (ysup ? 2 : 0));
+                  const T inv = TAB ? (T)__ldg(cf + kA[k] + bi)
+                                    : rcp(2 * st + a * (T)(xbnd ? 4 : (xsup ? 2 : 3)) +
+                                          bb * (T)(ybnd ? 4 : (ysup ? 2 : 3)));
+                  u0 = rhs * inv;
+                  rec1 = (xbnd ? (T)1 : (xsup ? (T)0 : (T)0.5)) * (u0 - Ux);
+                  rec2 = (ybnd ? (T)1 : (ysup ? (T)0 : (T)0.5)) * (u0 - Vy);
+                }
                 if (src_bnd) { rec1 -= xa0; rec2 -= ya0; }
                 // direction-dependent part of L(u; b_r): u1 = A1 + rec1, u2 = A2 + rec2, inflow traces U, V
                 //   r=1: 2a (U0 - u0) + (2a + 2/3 b) rec1 - 2/3 b V1   (2/3 sigma_t h rec1: epilogue)
@@ -643,12 +685,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 }
                 acc[4] = fma(wx[k], rec1, acc[4]);
                 acc[5] = fma(wy[k], rec2, acc[5]);
+                if constexpr (VAR == 3) { xs[k][3] = Ux; ys[k][3] = Vy; }
                 xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
                 ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
-                T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * 3;
+                T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * kTraceStride;
 #pragma unroll
                 for (int c = 0; c < NS; ++c) yp[c] = ys[k][c];
               }
@@ -726,7 +769,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
                                 const double *__restrict__ sigt, const double *__restrict__ qm,
                                 const double *__restrict__ p1ra, const double *__restrict__ sq1, int source,
                                 double *__restrict__ y) {
-  constexpr int NR = (VAR == 2) ? 6 : 4;
+  constexpr int NR = VAR == kP0 ? 2 : ((VAR >= 2) ? 6 : 4);
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   double s[NR];
@@ -758,14 +801,16 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   const double2 xa = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K);
   const double2 xb = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K + 2);
   double o0, o1, o2, o3;
-  if (VAR == 0) {
+  if constexpr (VAR == 0) {
     o0 = xa.x - s[0]; o1 = xa.y - s[1]; o2 = xb.x - s[2]; o3 = xb.y - s[3];
+  } else if constexpr (VAR == kP0) {
+    o0 = xa.x - s[0]; o1 = xa.y; o2 = xb.x; o3 = xb.y;   // P0-DG: the slope entries are carried by the identity
   } else {
     const double m = sse[K] * h * h;
     const double c = 2.0 / 3.0, sh = sigt[K] * h;
     const double Mw = qm[0], Ma = qm[1], Mb = qm[2], MOx = qm[3], MOy = qm[4];
     double S1 = 0, S2 = 0, p1 = 0, p2 = 0;
-    if (VAR == 2) {
+    if constexpr (VAR >= 2) {
       S1 = s[4]; S2 = s[5];
       if (source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; S1 -= p1; S2 -= p2; }
     }
@@ -773,7 +818,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
     double T1 = s[1] + (2 * Ma + c * Mb + c * sh * Mw) * A1 + c * MOy * A3;
     double T2 = s[2] + (2 * Mb + c * Ma + c * sh * Mw) * A2 + c * MOx * A3;
     const double T3 = s[3] - c * MOy * A1 - c * MOx * A2 + (c * (Ma + Mb) + (2.0 / 9.0) * sh * Mw) * A3;
-    if (VAR == 2) { T1 += c * sh * s[4]; T2 += c * sh * s[5]; }
+    if constexpr (VAR >= 2) { T1 += c * sh * s[4]; T2 += c * sh * s[5]; }
     o0 = xa.x - s[0];
     o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * T1;
     o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * T2;
@@ -804,7 +849,9 @@ static const void *kernel_for_variant(int variant, int apw) {
   switch (variant) {
     case LMDG_STD: return kernel_for<T, 0, TAB>(apw);
     case LMDG_LM: return kernel_for<T, 1, TAB>(apw);
-    default: return kernel_for<T, 2, TAB>(apw);
+    case LMDG_RLM: return kernel_for<T, 2, TAB>(apw);
+    case kRlmStar: return kernel_for<T, 3, TAB>(apw);
+    default: return kernel_for<T, kP0, TAB>(apw);
   }
 }
 
@@ -845,6 +892,10 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
         prep_kernel<T, 1><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
                                             qiso, src, sh, a.coef ? a.mat : nullptr);
         break;
+      case kP0:
+        prep_kernel<T, kP0><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra,
+                                              a.source, qiso, src, sh, a.coef ? a.mat : nullptr);
+        break;
       default:
         prep_kernel<T, 2><<<gs, bs, 0, s>>>(a.nx, a.h, a.eps, a.X, a.pd.sse, a.pd.sigt, a.pd.q, a.p1ra, a.source,
                                             qiso, src, sh, a.coef ? a.mat : nullptr);
@@ -883,6 +934,9 @@ cudaError_t launch_epilogue(int variant, int nx, int P, double h, const T *part,
       break;
     case LMDG_LM:
       epilogue_kernel<T, 1><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
+      break;
+    case kP0:
+      epilogue_kernel<T, kP0><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
       break;
     default:
       epilogue_kernel<T, 2><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);

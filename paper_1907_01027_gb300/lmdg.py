@@ -10,8 +10,8 @@ import numpy as np
 
 from . import buildlib as _build_mod
 
-STD, LM, RLM = 0, 1, 2
-VARIANTS = {"std": STD, "lm": LM, "rlm": RLM}
+STD, LM, RLM, P0 = 0, 1, 2, 3
+VARIANTS = {"std": STD, "lm": LM, "rlm": RLM, "p0": P0}
 FP64, FP32, FP32_BF16STORE = 0, 1, 2
 SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS = 1, 2, 4, 8
 ERR_TIMEOUT, ERR_NOTCONV = -6, -5
@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("device", ctypes.c_int),
-                ("suppress", ctypes.c_int)]
+                ("suppress", ctypes.c_int), ("recon", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -38,7 +38,8 @@ def test_invalid_arguments_rejected(L):
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
     assert _setup(L, p, eps=0.0) == -1
     assert _setup(L, p, eps=-1.0) == -1
-    assert _setup(L, p, variant=3) == -1
+    assert _setup(L, p, variant=4) == -1
+    assert _setup(L, p, variant=-1) == -1
     bad = uniform_problem(4, 4, 1.0, 1.0, 1.0)
     bad.sigma_a[3] = -0.1
     assert _setup(L, bad) == -1
@@ -82,3 +83,21 @@ def test_suppress_option_validated(L):
         rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
                           arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
         assert rc == -1, (variant, flag)
+
+
+def test_recon_option_validated(L):
+    """The three-cell reconstruction (RLMDG*) is RLMDG's only, takes 0 or 1 and excludes suppression."""
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
+    quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+    for variant, recon, supp in ((0, 1, 0), (1, 1, 0), (3, 1, 0), (2, 2, 0), (2, 1, 1)):
+        o = Options()
+        L.lmdg_default_options(ctypes.byref(o))
+        o.recon = recon
+        o.suppress = supp
+        h = ctypes.c_void_p()
+        rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
+        assert rc == -1, (variant, recon, supp)
