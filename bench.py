@@ -35,8 +35,8 @@ FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 # DRAM bytes (read + write) per launch of the FP32 non-storing sweep kernel, from one ncu capture of the
 # 512x512 S16 profiling case (bench.py --profile); the launch shape, hence the partial reductions per cell, is
 # the same at 1024x1024, so a full launch moves 4x these.  Must be re-measured whenever the kernel changes.
-SWEEP_DRAM_BYTES_512 = {"std": 18.665984e6 + 40.936960e6, "lm": 18.561024e6 + 9.046528e6,
-                        "rlm": 16.137216e6 + 82.065152e6}
+SWEEP_DRAM_BYTES_512 = {"std": 23.052288e6 + 45.057280e6, "lm": 22.993408e6 + 12.834304e6,
+                        "rlm": 23.395584e6 + 86.222592e6}
 
 
 def workload_config():
