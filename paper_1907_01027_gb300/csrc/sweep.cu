@@ -111,6 +111,26 @@ template <typename T, int NR> __device__ __forceinline__ void store_nr(T *dst, c
     }
   }
 }
+template <typename T, int NR> __device__ __forceinline__ void load_nr(T *dst, const T *src) {
+  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(src + q);
+      dst[q] = t.x; dst[q + 1] = t.y; dst[q + 2] = t.z; dst[q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2) {
+      if constexpr (sizeof(T) == 4) {
+        const float2 t = *reinterpret_cast<const float2 *>(src + q);
+        dst[q] = t.x; dst[q + 1] = t.y;
+      } else {
+        const double2 t = *reinterpret_cast<const double2 *>(src + q);
+        dst[q] = t.x; dst[q + 1] = t.y;
+      }
+    }
+  }
+}
 template <typename T, int NR> __device__ __forceinline__ void add_nr(T *acc, const T *src) {
   if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
 #pragma unroll
@@ -602,6 +622,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   acc[1] += Wx[k] * u1 * (T)pf[1];
                   acc[2] += Wy[k] * u2 * (T)pf[2];
                   acc[3] += W3a[k] * u3 * (T)pf[3];
+                } else if (k == 0) {   // the first direction sets the sums (no addition of zero)
+                  acc[0] = wl * u0;
+                  acc[1] = Wx[k] * u1;
+                  acc[2] = Wy[k] * u2;
+                  acc[3] = W3a[k] * u3;
                 } else {
                   acc[0] += wl * u0;
                   acc[1] += Wx[k] * u1;
@@ -724,9 +749,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       const int ii = sx > 0 ? x : n - 1 - x, jj = sy > 0 ? r : n - 1 - r;
       const size_t K = (size_t)jj * n + ii;
       T sum[NR];
-#pragma unroll
-      for (int q = 0; q < NR; ++q) sum[q] = 0;
-      for (int ww = 0; ww < W; ++ww) {
+      load_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W) * 32 + l) * NR);   // warp 0, then the others in order
+      for (int ww = 1; ww < W; ++ww) {
         add_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W + ww) * 32 + l) * NR);
       }
       T *dst = A.part + ((size_t)pq * nx + K) * NR;
@@ -781,9 +805,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
     T v[4][NR];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-#pragma unroll
-      for (int r = 0; r < NR; ++r) v[i][r] = 0;
-      add_nr<T, NR>(v[i], part + ((size_t)(p + i) * nx + K) * NR);
+      load_nr<T, NR>(v[i], part + ((size_t)(p + i) * nx + K) * NR);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -792,9 +814,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   }
   for (; p < P; ++p) {
     T v[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = 0;
-    add_nr<T, NR>(v, part + ((size_t)p * nx + K) * NR);
+    load_nr<T, NR>(v, part + ((size_t)p * nx + K) * NR);
 #pragma unroll
     for (int r = 0; r < NR; ++r) s[r] += (double)v[r];
   }
