@@ -223,7 +223,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   go->breakdown = false;
   for (int j = 0; j < m && j < max_it; ++j) {
     double *vj = V + (size_t)j * N;
-    CK(precond(z, vj, c->b11diag, c->nx, pmode, s));
+    CK(precond(z, vj, c->b11dinv, c->nx, pmode, s));
     if (int e = sweep_prec(c, fp32, z, w, 0, false, 0, s)) return e;
     // classical Gram-Schmidt, twice
     CK(mdot(V, N, j + 1, w, N, partial, hdev, 0, s));
@@ -268,7 +268,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   CK(cudaMemcpyAsync(ydev, c->red_h, sizeof(double) * k, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
   CK(maxpy(z, V, N, k, ydev, N, s));
-  CK(precond(d, z, c->b11diag, c->nx, pmode, s));
+  CK(precond(d, z, c->b11dinv, c->nx, pmode, s));
   CK(cudaStreamSynchronize(s));
   go->iters = k;
   return 0;
@@ -325,7 +325,7 @@ void lmdg_destroy(lmdg_ctx *c) {
   cudaSetDevice(c->dev);
   free_pd(c->d64);
   free_pd(c->d32);
-  cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11diag);
+  cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11dinv);
   cudaFree(c->sigma_a); cudaFree(c->qmom); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
   cudaFree(c->cellsrc); cudaFree(c->cellsh);
   cudaFree(c->rev); cudaFree(c->qadj64); cudaFree(c->qadj32); cudaFree(c->adj_buf);
@@ -472,6 +472,9 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     for (int r = 0; r < 3; ++r)
       bd[3 * K + r] = eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r];
 
+  std::vector<double> bdinv(bd.size());
+  for (size_t k = 0; k < bd.size(); ++k) bdinv[k] = 1.0 / bd[k];   // the preconditioner multiplies
+
   // opposite direction of every sorted direction (central symmetry, needed by the adjoint)
   std::vector<int> rev(na, 0);
   bool rev_ok = true;
@@ -496,7 +499,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
       (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qv)) ||
       (e = upload(&c->p1ra64, p1ra)) || (e = upload(&c->p1ra32, p1ra)) || (e = upload(&c->sq1, sq1)) ||
-      (e = upload(&c->b11diag, bd)) || (e = upload(&c->sigma_a, sa)) || (e = upload(&c->qmom, qm)))
+      (e = upload(&c->b11dinv, bdinv)) || (e = upload(&c->sigma_a, sa)) || (e = upload(&c->qmom, qm)))
     return fail(e);
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);

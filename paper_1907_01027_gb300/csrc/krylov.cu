@@ -4,11 +4,12 @@
 #include "lmdg_internal.h"
 #include "krylov.h"
 #include <atomic>
+#include <cstdint>
 
 namespace lmdg {
 
 namespace {
-constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kDotChunk = 8;         // vectors reduced per pass over w
 
@@ -19,7 +20,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 }  // namespace
 
-// partial[b * nv + i] = sum over this block's slice of V_i[k] * w[k], i < nv
+// partial[b * nv + i] = sum over this block's slice of V_i[k] * w[k], i < nv.  PAIRS: entries move as 16-byte
+// pairs (N, ldv even and 16-byte aligned vectors, as the [nx][4] Krylov vectors are); the summation order is fixed
+// by the launch shape.
+template <bool PAIRS>
 __global__ void mdot_kernel(const double *__restrict__ V, size_t ldv, int nv, const double *__restrict__ w,
                             size_t N, double *__restrict__ partial) {
   __shared__ double sh[kRedThreads / 32][kDotChunk];
@@ -29,11 +33,24 @@ __global__ void mdot_kernel(const double *__restrict__ V, size_t ldv, int nv, co
     double acc[kDotChunk];
 #pragma unroll
     for (int c = 0; c < kDotChunk; ++c) acc[c] = 0;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-      const double wk = w[k];
+    if (PAIRS) {
+      const double2 *w2 = reinterpret_cast<const double2 *>(w);
+      for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += (size_t)gridDim.x * blockDim.x) {
+        const double2 wk = w2[k];
 #pragma unroll
-      for (int c = 0; c < kDotChunk; ++c)
-        if (c < nc) acc[c] = fma(V[(size_t)(c0 + c) * ldv + k], wk, acc[c]);
+        for (int c = 0; c < kDotChunk; ++c)
+          if (c < nc) {
+            const double2 v = reinterpret_cast<const double2 *>(V + (size_t)(c0 + c) * ldv)[k];
+            acc[c] = fma(v.y, wk.y, fma(v.x, wk.x, acc[c]));
+          }
+      }
+    } else {
+      for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int c = 0; c < kDotChunk; ++c)
+          if (c < nc) acc[c] = fma(V[(size_t)(c0 + c) * ldv + k], wk, acc[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < kDotChunk; ++c) {
@@ -50,32 +67,48 @@ __global__ void mdot_kernel(const double *__restrict__ V, size_t ldv, int nv, co
   }
 }
 
-// out[i] = scale * sum_b partial[b * nv + i]   (+ out[i] if accumulate)
+// out[i] = sum_b partial[b * nv + i]   (+ out[i] if accumulate); one warp per output: lane l sums the blocks
+// b = l, l + 32, ... in order, then a fixed butterfly combines the lanes (deterministic)
 __global__ void mdot_fin_kernel(const double *__restrict__ partial, int nb, int nv, double *__restrict__ out,
                                 int accumulate) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= nv) return;
   double s = 0;
-  for (int b = 0; b < nb; ++b) s += partial[(size_t)b * nv + i];
-  out[i] = accumulate ? out[i] + s : s;
+  for (int b = lane; b < nb; b += 32) s += partial[(size_t)b * nv + i];
+  s = warp_sum(s);
+  if (lane == 0) out[i] = accumulate ? out[i] + s : s;
 }
 
-// w -= sum_i V_i coef_i
+// w -= sum_i V_i coef_i (pairs of entries per thread, coefficients staged in shared memory; nv <= 128)
 __global__ void maxpy_kernel(double *__restrict__ w, const double *__restrict__ V, size_t ldv, int nv,
                              const double *__restrict__ coef, size_t N) {
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-    double s = w[k];
-    for (int i = 0; i < nv; ++i) s = fma(-coef[i], V[(size_t)i * ldv + k], s);
-    w[k] = s;
+  __shared__ double cs[128];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = coef[i];
+  __syncthreads();
+  double2 *w2 = reinterpret_cast<double2 *>(w);
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += (size_t)gridDim.x * blockDim.x) {
+    double2 s = w2[k];
+    for (int i = 0; i < nv; ++i) {
+      const double2 v = reinterpret_cast<const double2 *>(V + (size_t)i * ldv)[k];
+      s.x = fma(-cs[i], v.x, s.x);
+      s.y = fma(-cs[i], v.y, s.y);
+    }
+    w2[k] = s;
   }
 }
 
-// y = x * (1 / *nrm)  (nrm on the device)
+// y = x * (1 / sqrt(*nrm2))  (nrm2 on the device; the reciprocal is formed once per block -- FP64 square root
+// and division are long instruction sequences on a part where FP64 is scarce)
 __global__ void scale_by_inv_kernel(double *__restrict__ y, const double *__restrict__ x,
                                     const double *__restrict__ nrm2, size_t N) {
-  const double inv = 1.0 / sqrt(*nrm2);
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
-    y[k] = x[k] * inv;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / sqrt(*nrm2);
+  __syncthreads();
+  const double inv = s_inv;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = reinterpret_cast<const double2 *>(x)[k];
+    reinterpret_cast<double2 *>(y)[k] = make_double2(v.x * inv, v.y * inv);
+  }
 }
 
 __global__ void axpby_kernel(double *__restrict__ y, double a, const double *__restrict__ x, double b, size_t N) {
@@ -83,17 +116,18 @@ __global__ void axpby_kernel(double *__restrict__ y, double a, const double *__r
     y[k] = fma(a, x[k], b * y[k]);
 }
 
-// y = Minv x for the right preconditioner diag(I, diag(B11))^-1 on [nx][4] vectors (mode 1), copy (mode 0)
+// y = Minv x for the right preconditioner diag(I, diag(B11))^-1 on [nx][4] vectors (mode 1), copy (mode 0);
+// dinv holds the reciprocal diagonal
 __global__ void precond_kernel(double *__restrict__ y, const double *__restrict__ x,
-                               const double *__restrict__ diag, int nx, int mode) {
+                               const double *__restrict__ dinv, int nx, int mode) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   double2 va = reinterpret_cast<const double2 *>(x)[2 * K];
   double2 vb = reinterpret_cast<const double2 *>(x)[2 * K + 1];
   if (mode == 1) {
-    va.y /= diag[3 * (size_t)K];
-    vb.x /= diag[3 * (size_t)K + 1];
-    vb.y /= diag[3 * (size_t)K + 2];
+    va.y *= dinv[3 * (size_t)K];
+    vb.x *= dinv[3 * (size_t)K + 1];
+    vb.y *= dinv[3 * (size_t)K + 2];
   }
   reinterpret_cast<double2 *>(y)[2 * K] = va;
   reinterpret_cast<double2 *>(y)[2 * K + 1] = vb;
@@ -221,21 +255,29 @@ static int grid_for(size_t N) {
   return (int)(g < 2048 ? (g == 0 ? 1 : g) : 2048);
 }
 
+static bool pairs_ok(size_t N, size_t ldv, const void *a, const void *b) {
+  return N % 2 == 0 && ldv % 2 == 0 && reinterpret_cast<uintptr_t>(a) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(b) % 16 == 0;
+}
+
 cudaError_t mdot(const double *V, size_t ldv, int nv, const double *w, size_t N, double *partial, double *out,
                  int accumulate, cudaStream_t s) {
   add_launches(2);
-  mdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, nv, w, N, partial);
-  mdot_fin_kernel<<<(nv + 127) / 128, 128, 0, s>>>(partial, kRedBlocks, nv, out, accumulate);
+  if (pairs_ok(N, ldv, V, w)) mdot_kernel<true><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, nv, w, N, partial);
+  else mdot_kernel<false><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, nv, w, N, partial);
+  mdot_fin_kernel<<<(nv + 3) / 4, 128, 0, s>>>(partial, kRedBlocks, nv, out, accumulate);
   return cudaGetLastError();
 }
 size_t mdot_partial_len(int nvmax) { return (size_t)kRedBlocks * nvmax; }
 
 cudaError_t maxpy(double *w, const double *V, size_t ldv, int nv, const double *coef, size_t N, cudaStream_t s) {
+  if (nv > 128 || !pairs_ok(N, ldv, V, w)) return cudaErrorInvalidValue;
   add_launches(1);
   maxpy_kernel<<<grid_for(N), 256, 0, s>>>(w, V, ldv, nv, coef, N);
   return cudaGetLastError();
 }
 cudaError_t scale_by_inv(double *y, const double *x, const double *nrm2, size_t N, cudaStream_t s) {
+  if (!pairs_ok(N, 0, x, y)) return cudaErrorInvalidValue;
   add_launches(1);
   scale_by_inv_kernel<<<grid_for(N), 256, 0, s>>>(y, x, nrm2, N);
   return cudaGetLastError();
@@ -245,9 +287,9 @@ cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cuda
   axpby_kernel<<<grid_for(N), 256, 0, s>>>(y, a, x, b, N);
   return cudaGetLastError();
 }
-cudaError_t precond(double *y, const double *x, const double *diag, int nx, int mode, cudaStream_t s) {
+cudaError_t precond(double *y, const double *x, const double *dinv, int nx, int mode, cudaStream_t s) {
   add_launches(1);
-  precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, diag, nx, mode);
+  precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, dinv, nx, mode);
   return cudaGetLastError();
 }
 cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,

@@ -4,18 +4,18 @@
 #include <cstddef>
 
 namespace lmdg {
-// out[i] (+)= sum_k V_i[k] w[k], i < nv; partial needs mdot_partial_len(nv) doubles
+// out[i] (+)= sum_k V_i[k] w[k], i < nv (N and ldv even); partial needs mdot_partial_len(nv) doubles
 cudaError_t mdot(const double *V, size_t ldv, int nv, const double *w, size_t N, double *partial, double *out,
                  int accumulate, cudaStream_t s);
 size_t mdot_partial_len(int nvmax);
-// w -= sum_i V_i coef_i (coef on the device)
+// w -= sum_i V_i coef_i (coef on the device, nv <= 128; N and ldv even)
 cudaError_t maxpy(double *w, const double *V, size_t ldv, int nv, const double *coef, size_t N, cudaStream_t s);
-// y = x / sqrt(*nrm2)
+// y = x / sqrt(*nrm2) (N even)
 cudaError_t scale_by_inv(double *y, const double *x, const double *nrm2, size_t N, cudaStream_t s);
 // y = a x + b y
 cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cudaStream_t s);
-// y = diag(I, diag)^-1 x on [nx][4] (mode 1) or y = x (mode 0)
-cudaError_t precond(double *y, const double *x, const double *diag, int nx, int mode, cudaStream_t s);
+// y = diag(I, 1/dinv)^-1 x on [nx][4] (mode 1) or y = x (mode 0); dinv = reciprocal diagonal
+cudaError_t precond(double *y, const double *x, const double *dinv, int nx, int mode, cudaStream_t s);
 // y = B11 u on [nx][3]; A4 = {Ax+, Ax-, Ay+, Ay-}
 cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
                       double *y, cudaStream_t s);

@@ -114,7 +114,7 @@ struct lmdg_ctx {
   double *p1ra64 = nullptr;                // [nx][2]
   float *p1ra32 = nullptr;
   double *sq1 = nullptr;                   // [nx][3] Sigma Q1
-  double *b11diag = nullptr;               // [nx][3] diagonal of B11 (Jacobi preconditioner)
+  double *b11dinv = nullptr;               // [nx][3] reciprocal diagonal of B11 (Jacobi preconditioner)
   double *sigma_a = nullptr;               // [nx] (B11 stencil)
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};   // sum of w |Omega_x| over Omega_x > 0 / < 0, likewise y
   double *qmom = nullptr;                  // device [5] quadrature moments (epilogue)
