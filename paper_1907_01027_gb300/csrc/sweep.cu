@@ -796,28 +796,40 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   constexpr int NR = VAR == kP0 ? 2 : ((VAR >= 2) ? 6 : 4);
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
+  // the partials in index order, four quadrant-groups' loads in flight at a time.  FP32 partials are summed in
+  // FP32 with Neumaier's compensation and converted once (sum + compensation in FP64): as accurate as an FP64
+  // sum, without a float-to-double conversion and an FP64 addition per partial (FP64 is the scarce pipe).
   double s[NR];
+  T hs[NR], hc[NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) s[r] = 0;
-  // the partials in index order, four quadrant-groups' loads in flight at a time
+  for (int r = 0; r < NR; ++r) { hs[r] = 0; hc[r] = 0; }
+  auto add = [&](const T *v) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if constexpr (sizeof(T) == 4) {
+        const T t = hs[r] + v[r];
+        hc[r] += (fabsf(hs[r]) >= fabsf(v[r])) ? ((hs[r] - t) + v[r]) : ((v[r] - t) + hs[r]);
+        hs[r] = t;
+      } else {
+        hs[r] += v[r];
+      }
+    }
+  };
   int p = 0;
   for (; p + 4 <= P; p += 4) {
     T v[4][NR];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      load_nr<T, NR>(v[i], part + ((size_t)(p + i) * nx + K) * NR);
-    }
+    for (int i = 0; i < 4; ++i) load_nr<T, NR>(v[i], part + ((size_t)(p + i) * nx + K) * NR);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int r = 0; r < NR; ++r) s[r] += (double)v[i][r];
+    for (int i = 0; i < 4; ++i) add(v[i]);
   }
   for (; p < P; ++p) {
     T v[NR];
     load_nr<T, NR>(v, part + ((size_t)p * nx + K) * NR);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) s[r] += (double)v[r];
+    add(v);
   }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) s[r] = sizeof(T) == 4 ? (double)hs[r] + (double)hc[r] : (double)hs[r];
   const double2 xa = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K);
   const double2 xb = *reinterpret_cast<const double2 *>(X + 4 * (size_t)K + 2);
   double o0, o1, o2, o3;
