@@ -1,5 +1,5 @@
-"""Degenerate and ragged sizes against the oracle: a single cell, meshes around the 32-row strip boundary,
-the smallest quadrature (S2, four directions), vacuum and inflow data."""
+"""Degenerate and ragged sizes against the oracle: a single cell, meshes around one and two 32-row strips and
+ragged last strips, the smallest quadrature (S2, four directions), vacuum and inflow data."""
 import numpy as np
 import pytest
 
@@ -10,7 +10,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("variant", ["std", "lm", "rlm"])
-@pytest.mark.parametrize("n,N", [(1, 2), (1, 4), (2, 2), (16, 4), (31, 4), (32, 2), (33, 4), (64, 2)])
+@pytest.mark.parametrize("n,N", [(1, 2), (1, 4), (2, 2), (3, 2), (16, 4), (31, 4), (32, 2), (33, 4), (63, 2),
+                                 (64, 2), (65, 2), (97, 2)])
 def test_edge_sizes(variant, n, N):
     from paper_1907_01027_gb300 import Context, SWEEP_SOURCE, SWEEP_FP32
     p = random_problem(n, N, 0.5, 200 + n + N)
