@@ -4,9 +4,10 @@
 A step is one pass of the whole path over the 1024 x 1024, S16 workload with 16 x 16-cell patches of
 sigma_s, sigma_a ~ U[0.1, 10] (seed 1907), q = 1, eps = 1, vacuum inflow: for each scheme (standard Q1-DG,
 LMDG, RLMDG) one lmdg_solve to a 1e-8 relative residual with FP32 sweeps inside FP64 iterative refinement
-(FP64 Arnoldi and residuals), including the recovery sweep that stores the angular unknowns.  The metric is
-transport-sweep cell-angle updates per second over the step (every sweep the solves run, FP32 and FP64);
-time to 1e-8 for the mixed and the FP64 solver is reported beside it.
+(FP64 Arnoldi, least squares and updates; residual sweeps in float-float, LMDG_RESID_F32X2), including the
+recovery sweep that stores the angular unknowns.  The metric is transport-sweep cell-angle updates per second
+over the step (every sweep the solves run); time to 1e-8 for this solver, for the same solver with FP64
+residual sweeps and for the FP64 solver is reported beside it, with the final residual recomputed in FP64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -185,6 +186,7 @@ def run_gpu(args, rank, ws, dist):
     import numpy as np
     import torch
     from paper_1907_01027_gb300 import Context, FP32, FP64, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
+    from paper_1907_01027_gb300 import RESID_F32X2, RESID_FP64
     from paper_1907_01027_gb300 import buildlib
     from workloads.problems import config4
 
@@ -193,7 +195,7 @@ def run_gpu(args, rank, ws, dist):
     buildlib.build()
     p = config4(eps=1.0)
     upd = p.nx * p.nang
-    ctxs = {v: Context(p, v, precision=FP32, tol=1e-8, device=local) for v in VARIANTS}
+    ctxs = {v: Context(p, v, precision=FP32, resid=RESID_F32X2, tol=1e-8, device=local) for v in VARIANTS}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(stats_acc=None):
@@ -227,7 +229,7 @@ def run_gpu(args, rank, ws, dist):
         dist.barrier()
     torch.cuda.synchronize()
     total_ms = sum(durations)
-    sweeps = sum(st["sweeps_fp32"] + st["sweeps_fp64"] for _, st in stats)
+    sweeps = sum(st["sweeps_fp32"] + st["sweeps_fp64"] + st["sweeps_f32x2"] for _, st in stats)
     updates = sweeps * upd
     total_ms, updates = aggregate(total_ms, updates, dist)
     value = updates / (total_ms / 1e3)
@@ -238,6 +240,8 @@ def run_gpu(args, rank, ws, dist):
     f32_n = sum(st["sweeps_fp32"] for _, st in stats)
     f64_ms = sum(st["sweep_ms_fp64"] for _, st in stats)
     f64_n = sum(st["sweeps_fp64"] for _, st in stats)
+    f2_ms = sum(st["sweep_ms_f32x2"] for _, st in stats)
+    f2_n = sum(st["sweeps_f32x2"] for _, st in stats)
     flops = sum(FLOPS_PER_UPDATE[v] * st["sweeps_fp32"] * upd for v, st in stats)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = flops / (f32_ms / 1e3) / 1e12 if f32_ms > 0 else None
@@ -252,12 +256,14 @@ def run_gpu(args, rank, ws, dist):
                 "peak_source": "FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                 "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n,
                 "flops_per_update": FLOPS_PER_UPDATE,
-                "fp64_sweep_avg_ms": f64_ms / max(1, f64_n), "fp64_sweeps": f64_n}
+                "f32x2_sweep_avg_ms": f2_ms / max(1, f2_n), "f32x2_sweeps": f2_n,
+                "fp64_sweep_avg_ms": f64_ms / max(1, f64_n) if f64_n else None, "fp64_sweeps": f64_n}
     clocks = clk.summary()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps / f64 refinement", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 sweeps, f32x2 (float-float) residual sweeps, f64 refinement", "data": "synthetic",
            "config": workload_config(), "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
 
     # time to 1e-8: mixed (from the timed region) vs FP64 (one solve each, after it)
@@ -266,7 +272,27 @@ def run_gpu(args, rank, ws, dist):
         mixed = [st for vv, st in stats if vv == v]
         ttr[v] = {"mixed_ms": sum(s["time_ms"] for s in mixed) / len(mixed),
                   "mixed_iters": mixed[-1]["iters"], "mixed_refinements": mixed[-1]["refinements"],
-                  "mixed_sweeps_fp32": mixed[-1]["sweeps_fp32"], "mixed_sweeps_fp64": mixed[-1]["sweeps_fp64"]}
+                  "mixed_sweeps_fp32": mixed[-1]["sweeps_fp32"], "mixed_sweeps_f32x2": mixed[-1]["sweeps_f32x2"],
+                  "mixed_resid": mixed[-1]["resid"] / mixed[-1]["resid0"]}
+        # the same solve's final residual recomputed with FP64 sweeps: ||K x - b'|| / ||b'||
+        xs, _, _, _ = ctxs[v].solve(want_x=True, want_phi=False, device=True)
+        r = ctxs[v].sweep(xs, flags=SWEEP_SOURCE)
+        b = ctxs[v].sweep(torch.zeros_like(xs), flags=SWEEP_SOURCE)
+        ttr[v]["mixed_resid_fp64_check"] = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+        # the mixed solver with FP64 residual sweeps
+        ctx = Context(p, v, precision=FP32, resid=RESID_FP64, tol=1e-8, device=local)
+        ctx.solve(want_x=False, want_phi=True, device=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ttr[v].update({"mixed_fp64resid_ms": e0.elapsed_time(e1), "mixed_fp64resid_status": rc,
+                       "mixed_fp64resid_sweeps_fp64": st["sweeps_fp64"],
+                       "fp64_residual_sweep_avg_ms": st["sweep_ms_fp64"] / max(1, st["sweeps_fp64"]),
+                       "f32x2_residual_sweep_avg_ms": mixed[-1]["sweep_ms_f32x2"] /
+                       max(1, mixed[-1]["sweeps_f32x2"])})
+        ctx.close()
     if not args.skip_fp64:
         for v in VARIANTS:
             ctx = Context(p, v, precision=FP64, tol=1e-8, device=local)
@@ -317,12 +343,12 @@ def run_gpu(args, rank, ws, dist):
     for k in range(max(1, args.steps)):
         for v in VARIANTS:
             t0 = time.perf_counter()
-            ctx = Context(p, v, precision=FP32, tol=1e-8, device=local)
+            ctx = Context(p, v, precision=FP32, resid=RESID_F32X2, tol=1e-8, device=local)
             _, phi, st, rc = ctx.solve(want_x=False, want_phi=True, device=False)
             ctx.close()
             torch.cuda.synchronize()
             e2e_ms += 1e3 * (time.perf_counter() - t0)
-            e2e_upd += (st["sweeps_fp32"] + st["sweeps_fp64"]) * upd
+            e2e_upd += (st["sweeps_fp32"] + st["sweeps_fp64"] + st["sweeps_f32x2"]) * upd
             if k == 0:
                 h2d += 8 * (3 * p.nang + 2 * p.nx + 4 * p.nx)
                 d2h += phi.nbytes
@@ -344,11 +370,11 @@ def run_gpu(args, rank, ws, dist):
 
 def run_profile(args):
     """Small case for ncu: 512x512 cells, S16, the bench media; per pass the three FP32 non-storing sweeps (as
-    inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2) and the three
-    FP64 source sweeps (as in the refinement residual); two rounds (sweep kernels 1-7 untimed, 8-14 for the
-    capture)."""
+    inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2), the three
+    FP64 source sweeps (the refinement residual of LMDG_RESID_FP64) and the three float-float source sweeps (that
+    of LMDG_RESID_F32X2); two rounds (sweep kernels 1-10 untimed, 11-20 for the capture)."""
     import torch
-    from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
+    from paper_1907_01027_gb300 import Context, FP32, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE, SWEEP_F32X2
     from workloads.problems import config4
     torch.cuda.set_device(0)
     p = config4(eps=1.0, n=512)
@@ -361,6 +387,8 @@ def run_profile(args):
         ctx["std"].sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
         for v in ("std", "lm", "rlm"):
             ctx[v].sweep(x, y, flags=SWEEP_SOURCE)
+        for v in ("std", "lm", "rlm"):
+            ctx[v].sweep(x, y, flags=SWEEP_SOURCE | SWEEP_F32X2)
         torch.cuda.synchronize()
     for c in ctx.values():
         c.close()

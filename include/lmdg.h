@@ -43,12 +43,20 @@ enum { LMDG_STD = 0, LMDG_LM = 1, LMDG_RLM = 2, LMDG_P0 = 3 };
  * FP32_BF16STORE: as FP32, and the angular unknowns written by storing sweeps are bfloat16. */
 enum { LMDG_FP64 = 0, LMDG_FP32 = 1, LMDG_FP32_BF16STORE = 2 };
 
+/* Arithmetic of the residual sweeps of the FP32 modes (lmdg_options.resid).  FP64: double.  F32X2: float-float
+ * -- each value the unevaluated sum of two floats (48 significant bits, relative error of each operation a few
+ * 2^-48 of its operands, float's exponent range), on the FP32 pipe.  The refinement itself (the update of x,
+ * the residual norms, GMRES) stays FP64 in both. */
+enum { LMDG_RESID_FP64 = 0, LMDG_RESID_F32X2 = 1 };
+
 /* lmdg_sweep flags */
 enum {
   LMDG_SWEEP_SOURCE = 1,   /* y = K x - b (affine map whose zero solves the reduced system) instead of y = K x */
   LMDG_SWEEP_FP32 = 2,     /* run the sweep in float (x, y stay double) */
   LMDG_SWEEP_STORE = 4,    /* also store the angular unknowns of this sweep in the context (see lmdg_get_psi) */
-  LMDG_HOST_PTRS = 8       /* x, y (and other vectors of the call) are host pointers */
+  LMDG_HOST_PTRS = 8,      /* x, y (and other vectors of the call) are host pointers */
+  LMDG_SWEEP_F32X2 = 16    /* run the sweep in float-float (see LMDG_RESID_F32X2); not with LMDG_SWEEP_FP32 or
+                              LMDG_SWEEP_STORE */
 };
 
 /* Errors */
@@ -98,6 +106,8 @@ typedef struct {
                           Section 4.1); not combined with suppress; default 0 (two-cell, Section 3.3.1).  Its
                           sweep amplifies along rays through optically thin cells (sigma_t h below about 0.01 over
                           hundreds of cells), where round-off then dominates */
+  int resid;           /* FP32 modes: arithmetic of the residual sweeps, LMDG_RESID_FP64 (default) or
+                          LMDG_RESID_F32X2 */
 } lmdg_options;
 
 typedef struct {
@@ -107,11 +117,13 @@ typedef struct {
   int sweeps_fp32;     /* full transport sweeps run in FP32 */
   double resid0;       /* reference norm: ||r_0|| = ||b - K x0|| (FP64), or ||b|| from an FP32 sweep when an
                           FP32 mode starts from zero */
-  double resid;        /* final ||b - K x|| from an FP64 sweep */
+  double resid;        /* final ||b - K x|| from a residual sweep (FP64, or float-float with LMDG_RESID_F32X2) */
   double time_ms;      /* wall time of the call (host clock) */
   double sweep_ms_fp64;/* device time inside FP64 sweep kernels (CUDA events around each launch) */
   double sweep_ms_fp32;/* device time inside FP32 sweep kernels */
   long long launches;  /* kernels launched by the call */
+  int sweeps_f32x2;    /* full transport sweeps run in float-float */
+  double sweep_ms_f32x2; /* device time inside float-float sweep kernels */
 } lmdg_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -4,8 +4,9 @@ The compute path is ``liblmdg.so`` (hand-written CUDA for sm_103a, C ABI in ``in
 is a thin ctypes binding over it.  There is no CPU fallback: importing :mod:`.lmdg` raises if the library is
 not built.
 """
-from .lmdg import (Context, LmdgError, build, STD, LM, RLM, FP64, FP32, FP32_BF16STORE, SWEEP_SOURCE, SWEEP_FP32,
-                   SWEEP_STORE, HOST_PTRS, VARIANTS)
+from .lmdg import (Context, LmdgError, build, STD, LM, RLM, P0, FP64, FP32, FP32_BF16STORE, SWEEP_SOURCE,
+                   SWEEP_FP32, SWEEP_STORE, SWEEP_F32X2, HOST_PTRS, RESID_FP64, RESID_F32X2, VARIANTS)
 
-__all__ = ["Context", "LmdgError", "build", "STD", "LM", "RLM", "FP64", "FP32", "FP32_BF16STORE", "SWEEP_SOURCE",
-           "SWEEP_FP32", "SWEEP_STORE", "HOST_PTRS", "VARIANTS"]
+__all__ = ["Context", "LmdgError", "build", "STD", "LM", "RLM", "P0", "FP64", "FP32", "FP32_BF16STORE",
+           "SWEEP_SOURCE", "SWEEP_FP32", "SWEEP_STORE", "SWEEP_F32X2", "HOST_PTRS", "RESID_FP64", "RESID_F32X2",
+           "VARIANTS"]

@@ -51,15 +51,41 @@ void harvest(lmdg_ctx *c, bool wait) {
   c->ev_pending = -1;
 }
 
+// Float-float copies of the problem data and coefficient tables, made from the FP64 ones on the first
+// float-float sweep.
+int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
+  if (c->d2.ox) return 0;
+  const size_t na = c->nang, nx = c->nx;
+  const size_t nq = c->q_layout == 2 ? na * nx * 4 : nx * 4;
+  const size_t nal = c->has_alpha ? na * 4 * (size_t)c->n * 2 : 0;
+  const size_t ntab = c->coef ? (size_t)c->nmat * c->ncls * c->ncoef : 0;
+  struct Item { const double *src; f2 **dst; size_t n; } items[] = {
+      {c->d64.ox, &c->d2.ox, na}, {c->d64.oy, &c->d2.oy, na}, {c->d64.w, &c->d2.w, na},
+      {c->d64.sigt, &c->d2.sigt, nx}, {c->d64.sse, &c->d2.sse, nx}, {c->d64.q, &c->d2.q, nq},
+      {c->d64.alpha, &c->d2.alpha, nal}, {c->p1ra64, &c->p1ra2, 2 * nx}, {c->coef, &c->coef2, ntab}};
+  for (auto &it : items) {
+    if (it.n == 0 || it.src == nullptr) continue;
+    if (cudaMalloc(it.dst, sizeof(f2) * it.n) != cudaSuccess) return LMDG_ERR_NOMEM;
+    CK(convert_to_f2(it.src, *it.dst, it.n, s));
+  }
+  return 0;
+}
+
 template <typename T>
 int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s) {
   SweepArgs<T> a{};
-  const bool f64 = sizeof(T) == 8;
+  constexpr int P = prec_of<T>();
+  const bool f64 = P == 0;
+  if constexpr (P == 2) {
+    if (store) return LMDG_ERR_ARG;   // float-float sweeps feed residuals only
+    if (int e = ensure_f2(c, s)) return e;
+  }
   a.n = c->n; a.nq = c->nq; a.nang = c->nang; a.nx = c->nx;
   a.h = (T)c->h; a.eps = (T)c->eps;
-  a.g = f64 ? c->g64 : c->g32;
-  if constexpr (sizeof(T) == 8) { a.pd = c->d64; a.p1ra = c->p1ra64; }
-  else { a.pd = c->d32; a.p1ra = c->p1ra32; }
+  a.g = P == 0 ? c->g64 : (P == 1 ? c->g32 : c->g2);
+  if constexpr (P == 0) { a.pd = c->d64; a.p1ra = c->p1ra64; }
+  else if constexpr (P == 1) { a.pd = c->d32; a.p1ra = c->p1ra32; }
+  else { a.pd = c->d2; a.p1ra = c->p1ra2; }
   a.q_per_angle = c->q_layout == 2;
   a.X = X;
   a.source = source;
@@ -73,21 +99,23 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.corr = nullptr;
   a.rev = c->rev;
   if (c->use_adj) {
-    if constexpr (sizeof(T) == 8) a.pd.q = c->qadj64;
-    else a.pd.q = c->qadj32;
+    if constexpr (P == 0) a.pd.q = c->qadj64;
+    else if constexpr (P == 1) a.pd.q = c->qadj32;
+    else a.pd.q = c->qadj2;
     a.pd.alpha = nullptr;
     a.q_per_angle = 0;
     a.p1ra = nullptr;
   }
-  if constexpr (sizeof(T) == 8) a.corr = c->corr;
+  if constexpr (P == 0) a.corr = c->corr;
   a.supp = c->supp;
   a.coef = nullptr; a.ncoef = 0; a.ncls = 0; a.cls = nullptr; a.matsh = nullptr; a.mat = nullptr;
-  // coefficient tables for the FP64 sweeps, where they replace FP64 reciprocals; the FP32 sweeps form the
-  // coefficients with the hardware reciprocal as fast as they would load them (measured at 1024^2 S16)
-  if constexpr (sizeof(T) == 8) {
-    if (c->coef) {
-      a.coef = c->coef; a.ncoef = c->ncoef; a.ncls = c->ncls; a.cls = c->cls; a.matsh = c->matsh; a.mat = c->mat;
-    }
+  // coefficient tables for the FP64 and float-float sweeps, where they replace reciprocals and Schur products;
+  // the FP32 sweeps form the coefficients with the hardware reciprocal as fast as they would load them
+  // (measured at 1024^2 S16)
+  if (c->coef) {
+    if constexpr (P == 0) a.coef = c->coef;
+    else if constexpr (P == 2) a.coef = c->coef2;
+    if (a.coef) { a.ncoef = c->ncoef; a.ncls = c->ncls; a.cls = c->cls; a.matsh = c->matsh; a.mat = c->mat; }
   }
   a.psi = nullptr;
   a.psi_bf16 = 0;
@@ -113,8 +141,8 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   }
   if (c->ev_pending >= 0) harvest(c, true);
   // the strip traces must hold the empty pattern: initially, after a change of precision (float words sit at
-  // other offsets) and after a sweep that stopped early
-  const int want = f64 ? 0 : 1;
+  // other offsets than double and float-float words) and after a sweep that stopped early
+  const int want = P == 1 ? 1 : 0;
   if (c->ytr_dirty || c->ytr_prec != want) {
     if (fill_u32(reinterpret_cast<unsigned *>(c->ytr), kTraceEmpty, c->ytr_words, s) != cudaSuccess)
       return LMDG_ERR_CUDA;
@@ -124,17 +152,23 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   CK(cudaEventRecord(c->ev0, s));
   CK(launch_sweep<T>(c->kvar, a, s));
   CK(cudaEventRecord(c->ev1, s));
-  c->ev_pending = f64 ? 0 : 1;
+  c->ev_pending = P;
+  c->part_prec = P;
   // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
   CK(launch_epilogue<T>(c->kvar, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
                         c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
-  if (f64) c->sweeps64++; else c->sweeps32++;
+  if (P == 0) c->sweeps64++;
+  else if (P == 1) c->sweeps32++;
+  else c->sweeps2++;
   return 0;
 }
 
-int sweep_prec(lmdg_ctx *c, int fp32, const double *X, double *y, int source, bool store, int bf16,
+// prec: 0 FP64, 1 FP32, 2 float-float
+int sweep_prec(lmdg_ctx *c, int prec, const double *X, double *y, int source, bool store, int bf16,
                cudaStream_t s) {
-  return fp32 ? do_sweep<float>(c, X, y, source, store, bf16, s) : do_sweep<double>(c, X, y, source, store, 0, s);
+  if (prec == 1) return do_sweep<float>(c, X, y, source, store, bf16, s);
+  if (prec == 2) return do_sweep<f2>(c, X, y, source, store, 0, s);
+  return do_sweep<double>(c, X, y, source, store, 0, s);
 }
 
 int check_error_word(lmdg_ctx *c, cudaStream_t s) {
@@ -168,6 +202,16 @@ __global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const doub
     o[1] += s[4] - (p1ra ? p1ra[2 * (size_t)K] : 0.0);
     o[2] += s[5] - (p1ra ? p1ra[2 * (size_t)K + 1] : 0.0);
   }
+}
+
+template <typename T>
+cudaError_t launch_phi(lmdg_ctx *c, const T *part, int Pn, const double *X, double *P, cudaStream_t s) {
+  const int bs = 256, gs = (c->nx + bs - 1) / bs;
+  add_launches(1);
+  if (c->variant == LMDG_LM) phi_kernel<T, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
+  else if (c->variant == LMDG_P0) phi_kernel<T, kP0><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, nullptr, P);
+  else phi_kernel<T, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
+  return cudaGetLastError();
 }
 
 int ensure_krylov(lmdg_ctx *c, int m) {
@@ -291,6 +335,7 @@ int lmdg_default_options(lmdg_options *o) {
   o->device = 0;
   o->suppress = 0;
   o->recon = 0;
+  o->resid = LMDG_RESID_FP64;
   return 0;
 }
 
@@ -325,6 +370,8 @@ void lmdg_destroy(lmdg_ctx *c) {
   cudaSetDevice(c->dev);
   free_pd(c->d64);
   free_pd(c->d32);
+  free_pd(c->d2);
+  cudaFree(c->p1ra2); cudaFree(c->coef2); cudaFree(c->qadj2);
   cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11dinv);
   cudaFree(c->sigma_a); cudaFree(c->qmom); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
   cudaFree(c->cellsrc); cudaFree(c->cellsh);
@@ -374,7 +421,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (opt) o = *opt;
   if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
       (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || (o.recon != 0 && o.recon != 1) ||
-      (o.recon && (variant != LMDG_RLM || o.suppress)))
+      (o.recon && (variant != LMDG_RLM || o.suppress)) ||
+      (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2))
     return LMDG_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
@@ -521,14 +569,17 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       }
     if ((e = upload(&c->supp, bits))) return fail(e);
   }
-  c->g64 = choose_geom(c->kvar, n, c->nq, true);
-  c->g32 = choose_geom(c->kvar, n, c->nq, false);
-  if (c->g64.units() == 0 || c->g32.units() == 0) return fail(LMDG_ERR_CUDA);
+  c->g64 = choose_geom(c->kvar, n, c->nq, 0);
+  c->g32 = choose_geom(c->kvar, n, c->nq, 1);
+  c->g2 = choose_geom(c->kvar, n, c->nq, 2);
+  if (c->g64.units() == 0 || c->g32.units() == 0 || c->g2.units() == 0) return fail(LMDG_ERR_CUDA);
   if (std::getenv("LMDG_VERBOSE"))
     std::fprintf(stderr, "lmdg: n=%d n_omega=%d variant=%d fp64 shape groups=%d warps=%d apw=%d | fp32 groups=%d "
-                 "warps=%d apw=%d\n", n, na, variant, c->g64.groups, c->g64.warps, c->g64.apw, c->g32.groups,
-                 c->g32.warps, c->g32.apw);
-  const size_t pe = std::max(part_elems(c->g64, c->nx), part_elems(c->g32, c->nx));
+                 "warps=%d apw=%d | f32x2 groups=%d warps=%d apw=%d\n", n, na, variant, c->g64.groups,
+                 c->g64.warps, c->g64.apw, c->g32.groups, c->g32.warps, c->g32.apw, c->g2.groups, c->g2.warps,
+                 c->g2.apw);
+  const size_t pe =
+      std::max({part_elems(c->g64, c->nx), part_elems(c->g32, c->nx), part_elems(c->g2, c->nx)});
   if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   const int strips = (n + 31) / 32;
   const size_t ytr_elems = (size_t)na * strips * n * kTraceStride;
@@ -537,7 +588,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   c->ytr_dirty = true;
   if (cudaMalloc(&c->cellsrc, sizeof(double) * 4 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMalloc(&c->cellsh, sizeof(double) * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
-  c->ctrl_words = 2 + (size_t)std::max(c->g64.units(), c->g32.units());
+  c->ctrl_words = 2 + (size_t)std::max({c->g64.units(), c->g32.units(), c->g2.units()});
   if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);
   // FP64 element-solve coefficient tables per (material = distinct sigma_t h, direction class = distinct
@@ -589,6 +640,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
 
 int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream) {
   if (!c || !x || !y) return LMDG_ERR_ARG;
+  if ((flags & LMDG_SWEEP_F32X2) && (flags & (LMDG_SWEEP_FP32 | LMDG_SWEEP_STORE))) return LMDG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(c->dev));
   const size_t N = 4 * (size_t)c->nx;
@@ -600,8 +652,9 @@ int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream)
     xd = c->vec[4];
     yd = c->vec[5];
   }
-  if (int e = sweep_prec(c, (flags & LMDG_SWEEP_FP32) ? 1 : 0, xd, yd, (flags & LMDG_SWEEP_SOURCE) ? 1 : 0,
-                         (flags & LMDG_SWEEP_STORE) != 0, 0, s))
+  const int prec = (flags & LMDG_SWEEP_FP32) ? 1 : ((flags & LMDG_SWEEP_F32X2) ? 2 : 0);
+  if (int e = sweep_prec(c, prec, xd, yd, (flags & LMDG_SWEEP_SOURCE) ? 1 : 0, (flags & LMDG_SWEEP_STORE) != 0, 0,
+                         s))
     return e;
   if (flags & LMDG_HOST_PTRS) CK(cudaMemcpyAsync(y, yd, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   return check_error_word(c, s);
@@ -635,17 +688,19 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
   const size_t N = 4 * (size_t)c->nx;
   const int fp32 = c->opt.precision != LMDG_FP64;
   const int bf16 = c->opt.precision == LMDG_FP32_BF16STORE;
+  // residual sweeps: FP64, or float-float in the FP32 modes when asked for
+  const int rprec = (fp32 && c->opt.resid == LMDG_RESID_F32X2) ? 2 : 0;
   double *X = c->vec[2], *R = c->vec[3], *D = c->vec[4];
-  c->sweeps64 = c->sweeps32 = 0;
+  c->sweeps64 = c->sweeps32 = c->sweeps2 = 0;
   harvest(c, true);
-  c->sweep_ms[0] = c->sweep_ms[1] = 0;
+  c->sweep_ms[0] = c->sweep_ms[1] = c->sweep_ms[2] = 0;
   const long long launches0 = launch_count();
   if (x0) CK(cudaMemcpyAsync(X, x0, sizeof(double) * N,
                              (flags & LMDG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(X, 0, sizeof(double) * N, s));
-  // r = -(K x - b), FP64, storing (the last one is the recovery sweep in FP64 mode)
+  // r = -(K x - b), storing in FP64 mode (the last one is then the recovery sweep)
   auto residual = [&](double *rn2) -> int {
-    if (int e = sweep_prec(c, 0, X, R, 1, !fp32, 0, s)) return e;
+    if (int e = sweep_prec(c, rprec, X, R, 1, !fp32, 0, s)) return e;
     CK(axpby(R, -1.0, R, 0.0, N, s));
     if (int e = check_error_word(c, s)) return e;
     return norm2(c, R, rn2, s);
@@ -691,19 +746,15 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     if (go.breakdown && rnew > c->opt.tol * r0 && rnew >= rn) { rn = rnew; status = LMDG_ERR_BREAKDOWN; break; }
     rn = rnew;
   }
-  // outputs: phi from the partial reductions of the last FP64 sweep (at the final x)
+  // outputs: phi from the partial reductions of the last residual sweep (at the final x)
   if (phi) {
     double *P = (flags & LMDG_HOST_PTRS) ? c->vec[5] : phi;
     if (c->variant == LMDG_STD) {
       CK(cudaMemcpyAsync(P, X, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    } else if (rprec == 2) {
+      CK(launch_phi(c, reinterpret_cast<const f2 *>(c->part), 4 * c->g2.groups, X, P, s));
     } else {
-      const int bs = 256, gs = (c->nx + bs - 1) / bs, Pn = 4 * c->g64.groups;
-      const double *part = reinterpret_cast<const double *>(c->part);
-      add_launches(1);
-      if (c->variant == LMDG_LM) phi_kernel<double, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
-      else if (c->variant == LMDG_P0) phi_kernel<double, kP0><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, nullptr, P);
-      else phi_kernel<double, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
-      CK(cudaGetLastError());
+      CK(launch_phi(c, reinterpret_cast<const double *>(c->part), 4 * c->g64.groups, X, P, s));
     }
     if (flags & LMDG_HOST_PTRS) CK(cudaMemcpyAsync(phi, P, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   }
@@ -719,12 +770,14 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     st->refinements = fp32 ? refine : 0;
     st->sweeps_fp64 = c->sweeps64;
     st->sweeps_fp32 = c->sweeps32;
+    st->sweeps_f32x2 = c->sweeps2;
     st->resid0 = r0;
     st->resid = rn;
     st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     harvest(c, true);
     st->sweep_ms_fp64 = c->sweep_ms[0];
     st->sweep_ms_fp32 = c->sweep_ms[1];
+    st->sweep_ms_f32x2 = c->sweep_ms[2];
     st->launches = launch_count() - launches0;
   }
   return status;
@@ -808,6 +861,7 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
     if (cudaMalloc(&c->adj_buf, sizeof(double) * (5 * N + 4 * nx)) != cudaSuccess) return LMDG_ERR_NOMEM;
     if (cudaMalloc(&c->qadj64, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
     if (cudaMalloc(&c->qadj32, sizeof(float) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (cudaMalloc(&c->qadj2, sizeof(f2) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
   }
   double *Xf = c->adj_buf, *Lam = c->adj_buf + N, *Y = c->adj_buf + 2 * N, *G = c->adj_buf + 3 * N;
   double *PhiF = c->adj_buf + 3 * N + 4 * nx, *PhiA = PhiF + N;   // scalar-flux moments (low-memory)
@@ -819,6 +873,7 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
   std::vector<float> qa32(qa.begin(), qa.end());
   CK(cudaMemcpyAsync(c->qadj64, qa.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->qadj32, qa32.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+  CK(convert_to_f2(c->qadj64, c->qadj2, N, s));
   CK(cudaMemcpyAsync(G, gh.data(), sizeof(double) * nx, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   lmdg_stats s1{}, s2{};
@@ -865,6 +920,7 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
     st->refinements += s2.refinements;
     st->sweeps_fp64 = s1.sweeps_fp64 + s2.sweeps_fp64 + 1 + (c->opt.precision != LMDG_FP64 ? 1 : 0);
     st->sweeps_fp32 = s1.sweeps_fp32 + s2.sweeps_fp32;
+    st->sweeps_f32x2 = s1.sweeps_f32x2 + s2.sweeps_f32x2;
     st->resid = std::max(s1.resid / std::max(s1.resid0, 1e-300), s2.resid / std::max(s2.resid0, 1e-300));
     st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }

@@ -6,11 +6,11 @@
 
 namespace lmdg {
 
-SweepGeom env_override(SweepGeom best, int nq, int n) {
+SweepGeom env_override(SweepGeom best, int nq, int n, int amax) {
   if (const char *e = std::getenv("LMDG_SWEEP_GEOM")) {
     int a = 0, b = 0, c = 0;
     if (std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a >= 1 && a <= nq && b >= 1 && b <= 8 && c >= 1 &&
-        c <= kMaxA && b * c >= (nq + a - 1) / a && (a - 1) * ((nq + a - 1) / a) < nq)
+        c <= amax && b * c >= (nq + a - 1) / a && (a - 1) * ((nq + a - 1) / a) < nq)
       best = SweepGeom{a, b, c, (n + 31) / 32};
   }
   return best;
@@ -25,16 +25,24 @@ SweepGeom env_override(SweepGeom best, int nq, int n) {
 //         directions per warp and 6 warps (2.08 against 2.15);
 //   FP64 (FP64-pipe bound): Q1-DG one direction per warp, 4 warps (15.2 against 16.8 with two directions and
 //         6 warps); LMDG and RLMDG two directions per warp, 3 warps (9.2, 17.5).
-SweepGeom choose_geom(int variant, int n, int nq, bool fp64) {
+//   float-float (FP32-pipe bound, FP64-like registers; at most two directions per warp, the instances
+//         compiled): Q1-DG one direction per warp, 4 warps (4.45 against 4.68 with 8 warps); LMDG and P0-DG two
+//         directions per warp, 4 warps (3.18 against 3.29 with 2 warps); RLMDG one direction per warp, 8 warps
+//         (5.32 against 5.96 with two directions and 6 warps).
+SweepGeom choose_geom(int variant, int n, int nq, int prec) {
   int apw, wmax;
-  if (fp64) { apw = variant == LMDG_STD ? 1 : 2; wmax = variant == LMDG_STD ? 4 : 3; }
-  else { apw = variant == LMDG_LM ? 2 : 1; wmax = variant == LMDG_LM ? 6 : 8; }
+  if (prec == 0) { apw = variant == LMDG_STD ? 1 : 2; wmax = variant == LMDG_STD ? 4 : 3; }
+  else if (prec == 2) {
+    const bool row0 = variant == LMDG_LM || variant == kP0;
+    apw = row0 ? 2 : 1;
+    wmax = (row0 || variant == LMDG_STD) ? 4 : 8;
+  } else { apw = variant == LMDG_LM ? 2 : 1; wmax = variant == LMDG_LM ? 6 : 8; }
   int G = (nq + apw * wmax - 1) / (apw * wmax);
   while (G > 1 && (G - 1) * ((nq + G - 1) / G) >= nq) --G;
   const int gsize = (nq + G - 1) / G;
   const int a = gsize < apw ? gsize : apw;
   const int W = (gsize + a - 1) / a;
-  return env_override(SweepGeom{G, W, a, (n + 31) / 32}, nq, n);
+  return env_override(SweepGeom{G, W, a, (n + 31) / 32}, nq, n, prec == 2 ? 2 : kMaxA);
 }
 
 }  // namespace lmdg

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <type_traits>
 #include "../../include/lmdg.h"
+#include "f32x2.cuh"
 
 namespace lmdg {
 
@@ -87,8 +89,14 @@ template <typename T>
 size_t sweep_smem_bytes(int variant, int warps, int apw);
 template <typename T>
 int sweep_blocks_per_sm(int variant, int warps, int apw);
-// launch shape for a problem (all CTAs resident when possible); LMDG_SWEEP_GEOM="groups,warps,apw" overrides
-SweepGeom choose_geom(int variant, int n, int nq, bool fp64);
+// Sweep arithmetic: 0 double, 1 float, 2 float-float (f2)
+template <typename T>
+constexpr int prec_of() { return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2); }
+
+// launch shape for a problem and sweep arithmetic prec; LMDG_SWEEP_GEOM="groups,warps,apw" overrides
+SweepGeom choose_geom(int variant, int n, int nq, int prec);
+// y[i] = x[i] rounded to float-float
+cudaError_t convert_to_f2(const double *x, f2 *y, size_t n, cudaStream_t s);
 
 // y = K x - source * b  from the partial reductions (sweep.cu); sigt = sigma_t per cell, qm = the quadrature
 // moments written by quad_moments
@@ -111,14 +119,16 @@ struct lmdg_ctx {
   int *perm_h = nullptr;                   // host copy
   lmdg::ProblemData<double> d64;
   lmdg::ProblemData<float> d32;
+  lmdg::ProblemData<lmdg::f2> d2;          // float-float copies (residual sweeps of the mixed-precision solve)
   double *p1ra64 = nullptr;                // [nx][2]
   float *p1ra32 = nullptr;
+  lmdg::f2 *p1ra2 = nullptr;
   double *sq1 = nullptr;                   // [nx][3] Sigma Q1
   double *b11dinv = nullptr;               // [nx][3] reciprocal diagonal of B11 (Jacobi preconditioner)
   double *sigma_a = nullptr;               // [nx] (B11 stencil)
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};   // sum of w |Omega_x| over Omega_x > 0 / < 0, likewise y
   double *qmom = nullptr;                  // device [5] quadrature moments (epilogue)
-  lmdg::SweepGeom g64{}, g32{};
+  lmdg::SweepGeom g64{}, g32{}, g2{};
   void *part = nullptr;                    // partial reductions (double-sized)
   void *ytr = nullptr;                     // inter-strip traces (double-sized)
   void *cellsrc = nullptr;                 // [nx][4] per-sweep cell inputs (double-sized)
@@ -127,7 +137,8 @@ struct lmdg_ctx {
   size_t ctrl_words = 0;
   size_t ytr_words = 0;                    // 32-bit words of ytr
   bool ytr_dirty = true;                   // ytr must be refilled with kTraceEmpty before the next sweep
-  int ytr_prec = -1;                       // precision (0 double, 1 float) of the last sweep using ytr
+  int ytr_prec = -1;                       // trace layout of the last sweep using ytr (0: 8-byte, 1: 4-byte)
+  int part_prec = -1;                      // arithmetic (0 double, 1 float, 2 float-float) of the last partials
   void *psi = nullptr;                     // stored angular unknowns
   int psi_kind = -1;                       // -1 none, 0 double, 1 float, 2 bf16
   size_t psi_elems = 0;
@@ -138,15 +149,16 @@ struct lmdg_ctx {
   double *red_h = nullptr;                 // pinned host mirror
   int red_len = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int ev_pending = -1;                     // precision of a recorded, not yet harvested sweep (-1 none)
-  double sweep_ms[2] = {0, 0};             // device time in FP64 / FP32 sweep kernels
+  int ev_pending = -1;                     // arithmetic of a recorded, not yet harvested sweep (-1 none)
+  double sweep_ms[3] = {0, 0, 0};          // device time in FP64 / FP32 / float-float sweep kernels
   long long launches = 0;
-  int sweeps64 = 0, sweeps32 = 0;
+  int sweeps64 = 0, sweeps32 = 0, sweeps2 = 0;
   // adjoint (standard scheme): opposite directions, detector source, solve-time switches
   int *rev = nullptr;                      // device [nang] sorted -> user index of -Omega
   bool rev_ok = false;                     // the quadrature is centrally symmetric
   double *qadj64 = nullptr;                // [nx][4] detector source g/eps (r = 0)
   float *qadj32 = nullptr;
+  lmdg::f2 *qadj2 = nullptr;
   double *adj_buf = nullptr;               // [3][N] forward solution, multiplier, scratch
   bool use_adj = false;                    // sweeps take the detector source and vacuum inflow
   bool no_store = false;                   // solve keeps the stored psi untouched
@@ -157,5 +169,6 @@ struct lmdg_ctx {
   int *cls = nullptr;                      // [nang] sorted index -> direction class
   double *matsh = nullptr;                 // [nmat] sigma_t h
   double *coef = nullptr;                  // [nmat][ncls][ncoef]
+  lmdg::f2 *coef2 = nullptr;               // the same, float-float
   unsigned *supp = nullptr;                // RLMDG suppression bits per cell, or null
 };

@@ -95,12 +95,21 @@ template <> __device__ __forceinline__ void copy_cell<double>(double *d4, double
   cp_async16(d4 + 2, s4 + 2);
   cp_async8(dh, sh);
 }
+template <> __device__ __forceinline__ void copy_cell<f2>(f2 *d4, f2 *dh, const f2 *s4, const f2 *sh) {
+  cp_async16(d4, s4);
+  cp_async16(d4 + 2, s4 + 2);
+  cp_async8(dh, sh);
+}
 
 // NR consecutive values (a cell's reduced moments) moved with the widest aligned vector accesses: the buffers
 // hold them at NR-element strides, so NR = 4 floats are 16-byte aligned, NR = 6 floats 8-byte aligned and
-// doubles 16-byte aligned.
+// doubles and float-float pairs (NR even) 16-byte aligned.
 template <typename T, int NR> __device__ __forceinline__ void store_nr(T *dst, const T *v) {
-  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+  if constexpr (is_f2<T>::value) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2)
+      *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q].hi, v[q].lo, v[q + 1].hi, v[q + 1].lo);
+  } else if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < NR; q += 4) *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
   } else {
@@ -112,7 +121,13 @@ template <typename T, int NR> __device__ __forceinline__ void store_nr(T *dst, c
   }
 }
 template <typename T, int NR> __device__ __forceinline__ void load_nr(T *dst, const T *src) {
-  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+  if constexpr (is_f2<T>::value) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2) {
+      const float4 t = *reinterpret_cast<const float4 *>(src + q);
+      dst[q] = f2(t.x, t.y); dst[q + 1] = f2(t.z, t.w);
+    }
+  } else if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < NR; q += 4) {
       const float4 t = *reinterpret_cast<const float4 *>(src + q);
@@ -132,7 +147,13 @@ template <typename T, int NR> __device__ __forceinline__ void load_nr(T *dst, co
   }
 }
 template <typename T, int NR> __device__ __forceinline__ void add_nr(T *acc, const T *src) {
-  if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
+  if constexpr (is_f2<T>::value) {
+#pragma unroll
+    for (int q = 0; q < NR; q += 2) {
+      const float4 t = *reinterpret_cast<const float4 *>(src + q);
+      acc[q] += f2(t.x, t.y); acc[q + 1] += f2(t.z, t.w);
+    }
+  } else if constexpr (sizeof(T) == 4 && NR % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < NR; q += 4) {
       const float4 t = *reinterpret_cast<const float4 *>(src + q);
@@ -153,8 +174,12 @@ template <typename T, int NR> __device__ __forceinline__ void add_nr(T *acc, con
 }
 
 template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size_t idx, T v, int bf16) {
-  if (bf16) reinterpret_cast<__nv_bfloat16 *>(psi)[idx] = __float2bfloat16((float)v);
-  else reinterpret_cast<T *>(psi)[idx] = v;
+  if constexpr (is_f2<T>::value) {
+    reinterpret_cast<float *>(psi)[idx] = v.hi;   // float-float sweeps do not store (the host refuses it)
+  } else {
+    if (bf16) reinterpret_cast<__nv_bfloat16 *>(psi)[idx] = __float2bfloat16((float)v);
+    else reinterpret_cast<T *>(psi)[idx] = v;
+  }
 }
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -167,7 +192,11 @@ __device__ __forceinline__ bool is_empty(float v) { return __float_as_uint(v) ==
 __device__ __forceinline__ bool is_empty(double v) {
   return (unsigned long long)__double_as_longlong(v) == (((unsigned long long)kTraceEmpty << 32) | kTraceEmpty);
 }
+__device__ __forceinline__ bool is_empty(f2 v) {
+  return __float_as_uint(v.hi) == kTraceEmpty && __float_as_uint(v.lo) == kTraceEmpty;
+}
 __device__ __forceinline__ float empty_value(float) { return __uint_as_float(kTraceEmpty); }
+__device__ __forceinline__ f2 empty_value(f2) { return f2(__uint_as_float(kTraceEmpty), __uint_as_float(kTraceEmpty)); }
 __device__ __forceinline__ double empty_value(double) {
   return __longlong_as_double((long long)(((unsigned long long)kTraceEmpty << 32) | kTraceEmpty));
 }
@@ -181,18 +210,43 @@ __device__ __forceinline__ double ld_relaxed_t(const double *p) {
   asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
   return v;
 }
+// a float-float trace moves as one 64-bit word (hi in the low half), so that it is read and written whole
+__device__ __forceinline__ f2 ld_relaxed_t(const f2 *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return f2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
+}
+template <typename T> __device__ __forceinline__ void st_trace(T *p, T v) { *p = v; }
+template <> __device__ __forceinline__ void st_trace<f2>(f2 *p, f2 v) {
+  *reinterpret_cast<unsigned long long *>(p) =
+      ((unsigned long long)__float_as_uint(v.lo) << 32) | (unsigned long long)__float_as_uint(v.hi);
+}
 
 // Sign flip by the bit pattern (an integer op instead of an FP64 multiply): m = 0 keeps v, m = 0x80000000 negates.
 __device__ __forceinline__ double flip(double v, unsigned m) {
   return __hiloint2double(__double2hiint(v) ^ (int)m, __double2loint(v));
 }
 __device__ __forceinline__ float flip(float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); }
+__device__ __forceinline__ f2 flip(f2 v, unsigned m) { return f2(flip(v.hi, m), flip(v.lo, m)); }
+
+template <typename T> __device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(kFull, v, 1); }
+template <> __device__ __forceinline__ f2 shfl_up1<f2>(f2 v) {
+  return f2(__shfl_up_sync(kFull, v.hi, 1), __shfl_up_sync(kFull, v.lo, 1));
+}
+// read-only load of a coefficient-table entry
+template <typename T> __device__ __forceinline__ T tload(const T *p) { return __ldg(p); }
+template <> __device__ __forceinline__ f2 tload<f2>(const f2 *p) {
+  const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+  return f2(t.x, t.y);
+}
 
 // With coefficient tables the sigma_t h slot of the staged cell data carries the material index as a bit pattern.
 __device__ __forceinline__ double mat_bits(int m, double) { return __longlong_as_double((long long)m); }
 __device__ __forceinline__ float mat_bits(int m, float) { return __int_as_float(m); }
+__device__ __forceinline__ f2 mat_bits(int m, f2) { return f2(__int_as_float(m), 0.0f); }
 __device__ __forceinline__ int mat_of(double v) { return (int)__double_as_longlong(v); }
 __device__ __forceinline__ int mat_of(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int mat_of(f2 v) { return __float_as_int(v.hi); }
 
 }  // namespace
 
@@ -311,7 +365,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   constexpr int NC = (VAR == 1 || P0) ? 1 : 9;   // table coefficients per (material, class)
   constexpr int C = kChunk;
   // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
-  constexpr bool kF64 = sizeof(T) == 8;
+  constexpr bool kF64 = std::is_same<T, double>::value;
   const bool use_corr = kF64 && A.corr != nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit, s_abort;
@@ -470,7 +524,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
             v = ld_relaxed_t(p);
           }
           yw[it] = v;
-          *p = empty_value(v);
+          st_trace(p, empty_value(v));
         }
       }
       wabort = __any_sync(kFull, ab) != 0;
@@ -530,7 +584,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         // LMDG: the slope traces from below (one per lane; every direction carries the same value)
         T yl1_in = 0;
         if (VAR == 1) {
-          yl1_in = __shfl_up_sync(kFull, yl1, 1);
+          yl1_in = shfl_up1(yl1);
           if (lane == 0) yl1_in = (ybnd || nA == 0) ? (T)0 : yws[1];
         }
         const T A13 = A1 + A3, A23 = A2 + A3;
@@ -542,7 +596,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
             constexpr int NSH = (VAR == 1 || P0) ? 1 : NS;
             T yin[NS];
 #pragma unroll
-            for (int c = 0; c < NSH; ++c) yin[c] = __shfl_up_sync(kFull, ys[k][c], 1);
+            for (int c = 0; c < NSH; ++c) yin[c] = shfl_up1(ys[k][c]);
             if (act) {
               if (lane == 0) {
 #pragma unroll
@@ -588,9 +642,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 T u0, u1, u2, u3;
                 if (TAB) {
                   const T *cfk = cf + kA[k];
-                  const T i1 = (T)__ldg(cfk), i2 = (T)__ldg(cfk + 1), p1 = (T)__ldg(cfk + 2), p2 = (T)__ldg(cfk + 3);
-                  const T q1 = (T)__ldg(cfk + 4), q2 = (T)__ldg(cfk + 5), e0 = (T)__ldg(cfk + 6), e1 = (T)__ldg(cfk + 7);
-                  const T e3 = (T)__ldg(cfk + 8);
+                  const T i1 = tload(cfk), i2 = tload(cfk + 1), p1 = tload(cfk + 2), p2 = tload(cfk + 3);
+                  const T q1 = tload(cfk + 4), q2 = tload(cfk + 5), e0 = tload(cfk + 6), e1 = tload(cfk + 7);
+                  const T e3 = tload(cfk + 8);
                   const T b0 = r0 - p1 * r1 - p2 * r2;
                   const T b3 = r3 + q1 * r1 + q2 * r2;
                   u0 = e0 * b0 - e1 * b3;
@@ -645,7 +699,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 const T U0 = xs[k][0], V0 = yin[0];
                 T rhs = c2a[k] * (U0 - A1) + (c2b[k] * (V0 - A2) + S);
                 if (src_bnd) rhs += c2a[k] * xa0 + c2b[k] * ya0;
-                const T u0 = rhs * (TAB ? (T)__ldg(cf + kA[k]) : rcp(2 * (a + bb + st)));
+                const T u0 = rhs * (TAB ? tload(cf + kA[k]) : rcp(2 * (a + bb + st)));
                 // direction-dependent part of L(u; b_1), L(u; b_2): 2a (U0 - u0), 2b (V0 - u0) (zero inflow traces
                 // outside the mesh)
                 if (use_corr) {
@@ -679,7 +733,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   const T Uxx = xs[k][3], Vyy = yin[3];
                   rhs = fma(a, g1x * Ux - g2x * Uxx, fma(bb, g1y * Vy - g2y * Vyy, rhs));
                   if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
-                  const T inv = TAB ? (T)__ldg(cf + kA[k] + stx + 3 * sty)
+                  const T inv = TAB ? tload(cf + kA[k] + stx + 3 * sty)
                                     : rcp(2 * st + a * (2 + cdx) + bb * (2 + cdy));
                   u0 = rhs * inv;
                   rec1 = f0x * u0 - (f1x * Ux - f2x * Uxx);
@@ -688,7 +742,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   rhs = fma(a, xsup ? (T)0 : Ux, fma(bb, ysup ? (T)0 : Vy, rhs));
                   if (src_bnd) rhs += 4 * (a * xa0 + bb * ya0);
                   const int bi = (xbnd ? 1 : (xsup ? 2 : 0)) + 3 * (ybnd ? 1 : (ysup ? 2 : 0));
-                  const T inv = TAB ? (T)__ldg(cf + kA[k] + bi)
+                  const T inv = TAB ? tload(cf + kA[k] + bi)
                                     : rcp(2 * st + a * (T)(xbnd ? 4 : (xsup ? 2 : 3)) +
                                           bb * (T)(ybnd ? 4 : (ysup ? 2 : 3)));
                   u0 = rhs * inv;
@@ -718,7 +772,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
               if (lane == 31 && has_above) {
                 T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * kTraceStride;
 #pragma unroll
-                for (int c = 0; c < NS; ++c) yp[c] = ys[k][c];
+                for (int c = 0; c < NS; ++c) st_trace(yp + c, ys[k][c]);
               }
             }
           }
@@ -799,6 +853,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   // the partials in index order, four quadrant-groups' loads in flight at a time.  FP32 partials are summed in
   // FP32 with Neumaier's compensation and converted once (sum + compensation in FP64): as accurate as an FP64
   // sum, without a float-to-double conversion and an FP64 addition per partial (FP64 is the scarce pipe).
+  // Float-float partials are summed in float-float and converted once.
   double s[NR];
   T hs[NR], hc[NR];
 #pragma unroll
@@ -868,11 +923,16 @@ static const void *kernel_ptr() {
 
 template <typename T, int VAR, bool TAB>
 static const void *kernel_for(int apw) {
-  switch (apw) {
-    case 1: return kernel_ptr<T, VAR, 1, TAB>();
-    case 2: return kernel_ptr<T, VAR, 2, TAB>();
-    case 3: return kernel_ptr<T, VAR, 3, TAB>();
-    default: return kernel_ptr<T, VAR, 4, TAB>();
+  // float-float sweeps: one or two directions per warp (choose_geom caps them there)
+  if constexpr (is_f2<T>::value) {
+    return apw == 1 ? kernel_ptr<T, VAR, 1, TAB>() : kernel_ptr<T, VAR, 2, TAB>();
+  } else {
+    switch (apw) {
+      case 1: return kernel_ptr<T, VAR, 1, TAB>();
+      case 2: return kernel_ptr<T, VAR, 2, TAB>();
+      case 3: return kernel_ptr<T, VAR, 3, TAB>();
+      default: return kernel_ptr<T, VAR, 4, TAB>();
+    }
   }
 }
 
@@ -887,7 +947,7 @@ static const void *kernel_for_variant(int variant, int apw) {
   }
 }
 
-// coefficient tables exist for the FP64 sweeps only
+// coefficient tables exist for the FP64 and float-float sweeps
 template <typename T>
 static const void *sweep_kernel_ptr(int variant, int apw, bool tab) {
   if constexpr (sizeof(T) == 8) {
@@ -977,17 +1037,35 @@ cudaError_t launch_epilogue(int variant, int nx, int P, double h, const T *part,
   return cudaGetLastError();
 }
 
+__global__ void to_f2_kernel(size_t n, const double *__restrict__ x, f2 *__restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = f2(x[i]);
+}
+
+cudaError_t convert_to_f2(const double *x, f2 *y, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  add_launches(1);
+  to_f2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
+  return cudaGetLastError();
+}
+
 template size_t sweep_smem_bytes<double>(int, int, int);
 template size_t sweep_smem_bytes<float>(int, int, int);
+template size_t sweep_smem_bytes<f2>(int, int, int);
 template int sweep_blocks_per_sm<double>(int, int, int);
 template int sweep_blocks_per_sm<float>(int, int, int);
+template int sweep_blocks_per_sm<f2>(int, int, int);
 template cudaError_t launch_sweep<double>(int, const SweepArgs<double> &, cudaStream_t);
 template cudaError_t launch_sweep<float>(int, const SweepArgs<float> &, cudaStream_t);
+template cudaError_t launch_sweep<f2>(int, const SweepArgs<f2> &, cudaStream_t);
 template cudaError_t launch_epilogue<double>(int, int, int, double, const double *, const double *, const double *,
                                              const double *, const double *, const double *, const double *, int,
                                              double *, cudaStream_t);
 template cudaError_t launch_epilogue<float>(int, int, int, double, const float *, const double *, const double *,
                                             const double *, const double *, const double *, const double *, int,
                                             double *, cudaStream_t);
+template cudaError_t launch_epilogue<f2>(int, int, int, double, const f2 *, const double *, const double *,
+                                         const double *, const double *, const double *, const double *, int,
+                                         double *, cudaStream_t);
 
 }  // namespace lmdg

@@ -13,7 +13,8 @@ from . import buildlib as _build_mod
 STD, LM, RLM, P0 = 0, 1, 2, 3
 VARIANTS = {"std": STD, "lm": LM, "rlm": RLM, "p0": P0}
 FP64, FP32, FP32_BF16STORE = 0, 1, 2
-SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS = 1, 2, 4, 8
+SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS, SWEEP_F32X2 = 1, 2, 4, 8, 16
+RESID_FP64, RESID_F32X2 = 0, 1
 ERR_TIMEOUT, ERR_NOTCONV = -6, -5
 
 
@@ -35,14 +36,15 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("device", ctypes.c_int),
-                ("suppress", ctypes.c_int), ("recon", ctypes.c_int)]
+                ("suppress", ctypes.c_int), ("recon", ctypes.c_int), ("resid", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("sweeps_fp64", ctypes.c_int),
                 ("sweeps_fp32", ctypes.c_int), ("resid0", ctypes.c_double), ("resid", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("sweep_ms_fp64", ctypes.c_double),
-                ("sweep_ms_fp32", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("sweep_ms_fp32", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("sweeps_f32x2", ctypes.c_int), ("sweep_ms_f32x2", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

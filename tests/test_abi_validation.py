@@ -101,3 +101,21 @@ def test_recon_option_validated(L):
         rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
                           arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
         assert rc == -1, (variant, recon, supp)
+
+
+def test_resid_option_validated(L):
+    """The residual arithmetic takes LMDG_RESID_FP64 (0) or LMDG_RESID_F32X2 (1) only."""
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
+    quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+    for resid in (-1, 2, 7):
+        o = Options()
+        L.lmdg_default_options(ctypes.byref(o))
+        assert o.resid == 0
+        o.resid = resid
+        h = ctypes.c_void_p()
+        rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, 0, ctypes.byref(o))
+        assert rc == -1, resid

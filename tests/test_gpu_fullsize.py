@@ -3,8 +3,8 @@
 * FP64 reduced-operator applications of all three schemes at 1024^2 cells, S16 (the benchmark workload), every
   output against the oracle at 1e-12 (the oracle applies B11 literally instead of assembling it).
 * Source (residual) mode at 256^2, S8 (eps = 1e-2) against the oracle's right-hand side.
-* FP32 against FP64 sweeps at 1024^2 (a property: agreement to FP32 accuracy), and the mixed-precision solve
-  against the FP64 solve on the 256^2 workload.
+* FP32 against FP64 sweeps at 1024^2 (a property: agreement to FP32 accuracy), float-float sweeps against the
+  oracle at 3e-11, and the mixed-precision solve against the FP64 solve on the 256^2 workload.
 """
 import numpy as np
 import pytest
@@ -23,7 +23,7 @@ def cfg4():
 
 @pytest.mark.parametrize("variant", ["std", "lm", "rlm"])
 def test_operator_apply_1024_s16(cfg4, variant):
-    from paper_1907_01027_gb300 import Context, SWEEP_FP32
+    from paper_1907_01027_gb300 import Context, SWEEP_FP32, SWEEP_F32X2
     p = cfg4
     ctx = Context(p, variant)
     x = np.random.default_rng(7).standard_normal((p.nx, 4))
@@ -33,6 +33,8 @@ def test_operator_apply_1024_s16(cfg4, variant):
     assert rel(y, ref) < 1e-12
     y32 = ctx.sweep(x, flags=SWEEP_FP32)
     assert rel(y32, y) < 1e-5
+    # float-float (the residual sweeps of the mixed solve with LMDG_RESID_F32X2), against the oracle
+    assert rel(ctx.sweep(x, flags=SWEEP_F32X2), ref) < 3e-11
     ctx.close()
 
 
