@@ -663,18 +663,19 @@ int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream)
 int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   if (!c || !psi) return LMDG_ERR_ARG;
   if (c->psi_kind < 0) return LMDG_ERR_STATE;
+  const int per = c->variant == LMDG_STD ? 4 : 1;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(c->dev));
   if (flags & LMDG_HOST_PTRS) {
     double *tmp = nullptr;
     if (cudaMalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
-    cudaError_t e1 = lmdg::to_double(tmp, c->psi, c->psi_kind, c->psi_elems, s);
+    cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->n, c->psi_elems, s);
     cudaError_t e2 = cudaMemcpyAsync(psi, tmp, sizeof(double) * c->psi_elems, cudaMemcpyDeviceToHost, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
     cudaFree(tmp);
     return (e1 || e2 || e3) ? LMDG_ERR_CUDA : 0;
   }
-  CK(lmdg::to_double(psi, c->psi, c->psi_kind, c->psi_elems, s));
+  CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->n, c->psi_elems, s));
   return 0;
 }
 

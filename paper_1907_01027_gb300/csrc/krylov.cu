@@ -237,11 +237,19 @@ __global__ void fill_u32_kernel(unsigned *__restrict__ p, unsigned v, size_t N) 
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) p[k] = v;
 }
 
-__global__ void to_double_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, size_t N) {
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-    if (kind == 1) y[k] = (double)reinterpret_cast<const float *>(x)[k];
-    else if (kind == 2) y[k] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
-    else y[k] = reinterpret_cast<const double *>(x)[k];
+// Stored angular unknowns to the user layout: the sweeps keep them column-major per direction, [u][i][j][per]
+// (a warp's 32 rows of one column contiguous); the user layout is row-major, [u][j][i][per], in double.
+__global__ void psi_to_user_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, int per, int n,
+                                   size_t N) {
+  const size_t nx = (size_t)n * n;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < N; o += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = o % per, cell = o / per;
+    const size_t u = cell / nx, K = cell - u * nx;
+    const size_t j = K / n, i = K - j * n;
+    const size_t k = (u * nx + i * n + j) * per + c;
+    if (kind == 1) y[o] = (double)reinterpret_cast<const float *>(x)[k];
+    else if (kind == 2) y[o] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
+    else y[o] = reinterpret_cast<const double *>(x)[k];
   }
 }
 
@@ -310,9 +318,9 @@ cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s) {
   fill_u32_kernel<<<grid_for(N), 256, 0, s>>>(p, v, N);
   return cudaGetLastError();
 }
-cudaError_t to_double(double *y, const void *x, int kind, size_t N, cudaStream_t s) {
+cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int n, size_t N, cudaStream_t s) {
   add_launches(1);
-  to_double_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, N);
+  psi_to_user_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, per, n, N);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, 
                               const double *Phi, const double *Lam, double *out, cudaStream_t s);
 // p[0..N) = v
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s);
-// y = (double) x, kind 0 double, 1 float, 2 bfloat16
-cudaError_t to_double(double *y, const void *x, int kind, size_t N, cudaStream_t s);
+// stored psi (column-major per direction, kind 0 double, 1 float, 2 bfloat16; per values per cell) to the user
+// layout [u][n*n][per] in double; N = directions * n * n * per
+cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int n, size_t N, cudaStream_t s);
 }  // namespace lmdg

@@ -51,7 +51,8 @@ struct SweepArgs {
   const T *p1ra;       // [nx][2] P1 r_alpha (RLMDG, source sweeps) or null
   int source;          // 1: add eps q and the inflow data alpha
   T *part;             // [4*groups][nx][NR] partial reductions, written once each
-  void *psi;           // storing sweep output or null (sorted->user order through perm)
+  void *psi;           // storing sweep output or null: [nang (user order, through perm)][n (column i)][n (row j)]
+                       // [4 standard, 1 low-memory], column-major cells so that a warp's stores coalesce
   int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
   const int *perm;     // [nang] sorted index -> user index
   T *ytr;              // [nang][strips][n][kTraceStride] strip-boundary traces, kTraceEmpty when unwritten
@@ -59,8 +60,8 @@ struct SweepArgs {
   long long spin_limit;
   const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
   const T *cellsh;     // [nx] sigma_t h
-  const double *corr;  // adjoint correlation mode: stored forward psi ([nang(user)][nx][4] standard, [nang][nx]
-                       // low-memory); the reduction becomes sum_l w_l u_l,r psi_rev(l),r (r = 0 only for LMDG)
+  const double *corr;  // adjoint correlation mode: stored forward psi (layout of psi, double); the reduction
+                       // becomes sum_l w_l u_l,r psi_rev(l),r (r = 0 only for LMDG)
   const int *rev;      // [nang] sorted index -> user index of the opposite direction (corr mode)
   // Coefficient tables (FP64 sweeps; null: coefficients computed in the kernel).  With them, cellsh carries the
   // cell's material index and coef[(material * ncls + class) * ncoef + c] the solve coefficients of that

@@ -173,6 +173,19 @@ template <typename T, int NR> __device__ __forceinline__ void add_nr(T *acc, con
   }
 }
 
+// the four Legendre coefficients of a standard-scheme cell: one 16-byte store (float) or two (double)
+template <typename T> __device__ __forceinline__ void store_psi4(void *psi, size_t idx, T a, T b, T c, T d) {
+  if constexpr (std::is_same<T, float>::value) {
+    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(psi) + idx) = make_float4(a, b, c, d);
+  } else if constexpr (std::is_same<T, double>::value) {
+    double2 *p = reinterpret_cast<double2 *>(reinterpret_cast<double *>(psi) + idx);
+    p[0] = make_double2(a, b);
+    p[1] = make_double2(c, d);
+  } else {
+    float *p = reinterpret_cast<float *>(psi) + idx;   // float-float sweeps do not store (the host refuses it)
+    p[0] = a.hi; p[1] = b.hi; p[2] = c.hi; p[3] = d.hi;
+  }
+}
 template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size_t idx, T v, int bf16) {
   if constexpr (is_f2<T>::value) {
     reinterpret_cast<float *>(psi)[idx] = v.hi;   // float-float sweeps do not store (the host refuses it)
@@ -548,6 +561,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         const bool act = row_ok && x >= 0 && x < n;
         const int i = sx > 0 ? x : n - 1 - x;
         const int K = act ? j * n + i : 0;
+        // stored angular unknowns (and the adjoint's correlation input) are column-major, [i][j]: the warp's 32
+        // rows of one column are contiguous, so its psi stores coalesce
+        const int Kt = act ? i * n + j : 0;
         const bool xbnd = (x == 0);
         const bool ybnd = (strip == 0 && lane == 0);
         const T *yws = yup + ((size_t)warp * APW * C + s) * NS;   // + k * C * NS: direction k's inflow (lane 0)
@@ -671,7 +687,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 if (use_corr) {
                   // adjoint correlation: this sweep's psi (the multiplier of the opposite direction) times the
                   // stored forward psi of that opposite direction, per Legendre moment
-                  const double *pf = A.corr + ((size_t)cA[k] * nx + K) * 4;
+                  const double *pf = A.corr + ((size_t)cA[k] * nx + Kt) * 4;
                   acc[0] += wl * u0 * (T)pf[0];
                   acc[1] += Wx[k] * u1 * (T)pf[1];
                   acc[2] += Wy[k] * u2 * (T)pf[2];
@@ -689,10 +705,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-                if (A.psi) {
-                  T *pp = reinterpret_cast<T *>(A.psi) + ((size_t)uA[k] * nx + K) * 4;
-                  pp[0] = u0; pp[1] = flip(u1, mx); pp[2] = flip(u2, my); pp[3] = flip(u3, mxy);
-                }
+                if (A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * nx + Kt) * 4, u0, flip(u1, mx), flip(u2, my),
+                                         flip(u3, mxy));
               } else if constexpr (VAR == 1 || P0) {
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
                 //   rhs = S + 2a (U0 - A1) + 2b (V0 - A2), U0 / V0 the mean inflow traces (alpha on the boundary)
@@ -703,7 +717,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 // direction-dependent part of L(u; b_1), L(u; b_2): 2a (U0 - u0), 2b (V0 - u0) (zero inflow traces
                 // outside the mesh)
                 if (use_corr) {
-                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
+                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
                 } else {
                   acc[0] = fma(wl, u0, acc[0]);
                   if constexpr (!P0) {
@@ -719,7 +733,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   ys[k][0] = u0 + A2;
                   ys[k][1] = A13;
                 }
-                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
+                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               } else {
                 // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
                 //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
@@ -755,7 +769,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 //   r=2: 2b (V0 - u0) + (2b + 2/3 a) rec2 - 2/3 a U1
                 //   r=3: 2/3 a (U1 - rec2) + 2/3 b (V1 - rec1)
                 if (use_corr) {
-                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + K];
+                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
                 } else {
                   acc[0] = fma(wl, u0, acc[0]);
                   acc[1] = fma(nWxb[k], V1, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
@@ -767,7 +781,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 if constexpr (VAR == 3) { xs[k][3] = Ux; ys[k][3] = Vy; }
                 xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
                 ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
-                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + K, u0, A.psi_bf16);
+                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
                 T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * kTraceStride;

@@ -148,3 +148,20 @@ def test_spin_limit_reports_timeout_and_context_survives():
     y = ok.sweep(np.ones((p.nx, 4)))
     assert np.all(np.isfinite(y))
     ok.close()
+
+
+@pytest.mark.parametrize("n", [37, 70])
+def test_storing_sweep_psi_multistrip(n):
+    """A storing source sweep keeps psi_l = L^-1 (M Phi + Q) (the recovery of eq-sndg-final-sweep) on meshes of
+    two and three 32-row strips with a ragged last one, FP64 and FP32, read back in the user layout."""
+    from paper_1907_01027_gb300 import SWEEP_FP32, SWEEP_SOURCE, SWEEP_STORE
+    p = random_problem(n, 4, 1.0, 60 + n)
+    so = SweepOracle(p)
+    ctx = _ctx(p, "std")
+    x = np.random.default_rng(n).standard_normal((p.nx, 4))
+    ref = so.recover_std(x)
+    ctx.sweep(x, flags=SWEEP_SOURCE | SWEEP_STORE)
+    assert rel(ctx.get_psi(), ref) < 1e-12
+    ctx.sweep(x, flags=SWEEP_SOURCE | SWEEP_STORE | SWEEP_FP32)
+    assert rel(ctx.get_psi(), ref) < 1e-5
+    ctx.close()
