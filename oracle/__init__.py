@@ -14,9 +14,13 @@ Two independent implementations of what the method computes:
   Sigma, B11 and R applied matrix-free, transport sweeps as block lower-triangular solves in upwind order,
   the reduced systems eq-sndg-phi / eq-lmdg-reducemat / eq-rlmdg-reducemat solved by a library Krylov
   method, and the recovery steps.  Any mesh size.
+* :mod:`oracle.slab1d` -- the slab-geometry versions of the schemes (Section 4.1), assembled as trial/test
+  restrictions of the 1D P1 form and solved directly: a cross-check of the scheme readings against the
+  paper's printed 1D errors.
 
 Pins (``tests/test_oracle_*.py``): quadrature moments, Appendix A integrals against closed forms, exact
 reproduction of states that lie in each trial space, particle balance, B11 symmetry/definiteness,
 convergence orders of Table tab-2d-aniso, the diffusion limit of Example examp-2ddifflim and the
-nine-point limit stencil of Section 3.1, and sweep-vs-dense agreement on tiny meshes.
+nine-point limit stencil of Section 3.1, sweep-vs-dense agreement on tiny meshes, and the slab Tables
+tab-1d-aniso and tab-1d-eps10-5.
 """
