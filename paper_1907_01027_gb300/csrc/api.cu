@@ -269,17 +269,25 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
     double *vj = V + (size_t)j * N;
     CK(precond(z, vj, c->b11dinv, c->nx, pmode, s));
     if (int e = sweep_prec(c, fp32, z, w, 0, false, 0, s)) return e;
-    // classical Gram-Schmidt, twice
+    // classical Gram-Schmidt, twice in FP64 solves; once in the FP32 inner cycles of the refinement, whose
+    // operator is exact to FP32 only and whose target (inner_tol, 1e-4) lies far above the orthogonality a
+    // single pass keeps -- the FP64 or float-float residual that follows each cycle is exact regardless
+    const bool twice = !fp32;
     CK(mdot(V, N, j + 1, w, N, partial, hdev, 0, s));
     CK(maxpy(w, V, N, j + 1, hdev, N, s));
-    CK(mdot(V, N, j + 1, w, N, partial, h2dev, 0, s));
-    CK(maxpy(w, V, N, j + 1, h2dev, N, s));
+    if (twice) {
+      CK(mdot(V, N, j + 1, w, N, partial, h2dev, 0, s));
+      CK(maxpy(w, V, N, j + 1, h2dev, N, s));
+    }
     CK(mdot(w, N, 1, w, N, partial, h2dev + j + 1, 0, s));
     CK(cudaMemcpyAsync(c->red_h, hdev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(c->red_h + (m + 2), h2dev, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    if (twice)
+      CK(cudaMemcpyAsync(c->red_h + (m + 2), h2dev, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+    else
+      CK(cudaMemcpyAsync(c->red_h + (m + 2) + j + 1, h2dev + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (int e = check_error_word(c, s)) return e;   // synchronises
     double *col = &H[(size_t)j * (m + 1)];
-    for (int i = 0; i <= j; ++i) col[i] = c->red_h[i] + c->red_h[m + 2 + i];
+    for (int i = 0; i <= j; ++i) col[i] = c->red_h[i] + (twice ? c->red_h[m + 2 + i] : 0.0);
     const double hn = std::sqrt(std::max(0.0, c->red_h[m + 2 + j + 1]));
     col[j + 1] = hn;
     if (!std::isfinite(hn)) return LMDG_ERR_BREAKDOWN;
