@@ -36,8 +36,8 @@ FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 # DRAM bytes (read + write) per launch of the FP32 non-storing sweep kernel, from one ncu capture of the
 # 512x512 S16 profiling case (bench.py --profile); the launch shape, hence the partial reductions per cell, is
 # the same at 1024x1024, so a full launch moves 4x these.  Must be re-measured whenever the kernel changes.
-SWEEP_DRAM_BYTES_512 = {"std": 23.049472e6 + 45.492736e6, "lm": 22.998272e6 + 12.680192e6,
-                        "rlm": 23.366656e6 + 85.650944e6}
+SWEEP_DRAM_BYTES_512 = {"std": 23.055616e6 + 45.447680e6, "lm": 22.998784e6 + 12.470528e6,
+                        "rlm": 23.408896e6 + 85.924352e6}
 
 
 def workload_config():

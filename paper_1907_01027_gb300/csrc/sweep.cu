@@ -197,6 +197,15 @@ template <typename T> __device__ __forceinline__ void store_psi0(void *psi, size
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Polling of a strip trace that has not arrived: sleeps doubling from kPollNsMin to kPollNsMax between polls (a
+// trace is late by a fraction of a chunk in the steady wavefront, by hundreds of steps while it fills), and a
+// look at the error word every kAbortEvery polls.
+#ifndef LMDG_POLL_NS_MAX
+#define LMDG_POLL_NS_MAX 256
+#endif
+constexpr unsigned kPollNsMin = 16, kPollNsMax = LMDG_POLL_NS_MAX;
+constexpr long long kAbortEvery = 64;
+
 // Strip-boundary traces carry their own readiness: the buffer holds the NaN pattern kTraceEmpty (every 32-bit
 // word 0xFFF7FFF7, never produced by arithmetic, whose NaNs are canonical) until the producing lane stores
 // the value, and the consuming warp writes the pattern back after reading it.  Aligned 32/64-bit stores are
@@ -369,8 +378,10 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 #endif
 
 // TAB: the element-solve coefficients come from the FP64 tables (per material and direction class; FP64
-// instances only), else they are formed in the kernel from sigma_t h.
-template <typename T, int VAR, int APW, bool TAB>
+// instances only), else they are formed in the kernel from sigma_t h.  LEAN: the homogeneous, non-storing sweep
+// of the GMRES iterations (no source, inflow data, stored unknowns or correlation), compiled without the
+// per-step tests for them (FP32 instances).
+template <typename T, int VAR, int APW, bool TAB, bool LEAN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr bool P0 = VAR == kP0;         // P0-DG: the LMDG row-0 solve without slopes
   constexpr int NR = P0 ? 2 : ((VAR >= 2) ? 6 : 4);   // reduced values per cell
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   constexpr int C = kChunk;
   // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
   constexpr bool kF64 = std::is_same<T, double>::value;
-  const bool use_corr = kF64 && A.corr != nullptr;
+  const bool use_corr = kF64 && !LEAN && A.corr != nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit, s_abort;
 
@@ -507,7 +518,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   cp_async_wait_all();
   __syncthreads();
 
-  const bool src_bnd = A.source && A.pd.alpha;
+  const bool src_bnd = !LEAN && A.source && A.pd.alpha;
 
   for (int cc = 0; cc < nchunks; ++cc) {
     const int t0 = cc * C;
@@ -527,13 +538,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         if (p) {
           T v = pre[q];
           long long spins = 0;
+          unsigned sleep_ns = kPollNsMin;
           while (is_empty(v)) {
-            if (++spins > A.spin_limit || ld_relaxed(&A.ctrl[1]) != 0u) {
+            // the error word (one line every waiter on the GPU reads) is checked every kAbortEvery polls only
+            ++spins;
+            if (spins > A.spin_limit || ((spins & (kAbortEvery - 1)) == 0 && ld_relaxed(&A.ctrl[1]) != 0u)) {
               atomicExch(&A.ctrl[1], 1u);
               ab = 1;
               break;
             }
-            __nanosleep(20);
+            __nanosleep(sleep_ns);
+            if (sleep_ns < kPollNsMax) sleep_ns <<= 1;
             v = ld_relaxed_t(p);
           }
           yw[it] = v;
@@ -635,7 +650,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
               }
               T S = S0;
               const T *qp = nullptr;
-              if (A.source && A.q_per_angle) {
+              if (!LEAN && A.source && A.q_per_angle) {
                 qp = A.pd.q + ((size_t)ang[k] * nx + K) * 4;
                 S += 2 * h * A.eps * qp[0];
               }
@@ -705,7 +720,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-                if (A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * nx + Kt) * 4, u0, flip(u1, mx), flip(u2, my),
+                if (!LEAN && A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * nx + Kt) * 4, u0, flip(u1, mx), flip(u2, my),
                                          flip(u3, mxy));
               } else if constexpr (VAR == 1 || P0) {
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
@@ -733,7 +748,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   ys[k][0] = u0 + A2;
                   ys[k][1] = A13;
                 }
-                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
+                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               } else {
                 // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
                 //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
@@ -781,7 +796,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 if constexpr (VAR == 3) { xs[k][3] = Ux; ys[k][3] = Vy; }
                 xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
                 ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
-                if (A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
+                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
                 T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * kTraceStride;
@@ -930,50 +945,54 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(o2, o3);
 }
 
-template <typename T, int VAR, int APW, bool TAB>
+template <typename T, int VAR, int APW, bool TAB, bool LEAN>
 static const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW, TAB>);
+  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW, TAB, LEAN>);
 }
 
-template <typename T, int VAR, bool TAB>
+template <typename T, int VAR, bool TAB, bool LEAN>
 static const void *kernel_for(int apw) {
   // float-float sweeps: one or two directions per warp (choose_geom caps them there)
   if constexpr (is_f2<T>::value) {
-    return apw == 1 ? kernel_ptr<T, VAR, 1, TAB>() : kernel_ptr<T, VAR, 2, TAB>();
+    return apw == 1 ? kernel_ptr<T, VAR, 1, TAB, LEAN>() : kernel_ptr<T, VAR, 2, TAB, LEAN>();
   } else {
     switch (apw) {
-      case 1: return kernel_ptr<T, VAR, 1, TAB>();
-      case 2: return kernel_ptr<T, VAR, 2, TAB>();
-      case 3: return kernel_ptr<T, VAR, 3, TAB>();
-      default: return kernel_ptr<T, VAR, 4, TAB>();
+      case 1: return kernel_ptr<T, VAR, 1, TAB, LEAN>();
+      case 2: return kernel_ptr<T, VAR, 2, TAB, LEAN>();
+      case 3: return kernel_ptr<T, VAR, 3, TAB, LEAN>();
+      default: return kernel_ptr<T, VAR, 4, TAB, LEAN>();
     }
   }
 }
 
-template <typename T, bool TAB>
+template <typename T, bool TAB, bool LEAN>
 static const void *kernel_for_variant(int variant, int apw) {
   switch (variant) {
-    case LMDG_STD: return kernel_for<T, 0, TAB>(apw);
-    case LMDG_LM: return kernel_for<T, 1, TAB>(apw);
-    case LMDG_RLM: return kernel_for<T, 2, TAB>(apw);
-    case kRlmStar: return kernel_for<T, 3, TAB>(apw);
-    default: return kernel_for<T, kP0, TAB>(apw);
+    case LMDG_STD: return kernel_for<T, 0, TAB, LEAN>(apw);
+    case LMDG_LM: return kernel_for<T, 1, TAB, LEAN>(apw);
+    case LMDG_RLM: return kernel_for<T, 2, TAB, LEAN>(apw);
+    case kRlmStar: return kernel_for<T, 3, TAB, LEAN>(apw);
+    default: return kernel_for<T, kP0, TAB, LEAN>(apw);
   }
 }
 
-// coefficient tables exist for the FP64 and float-float sweeps
+// coefficient tables exist for the FP64 and float-float sweeps; lean instances for FP32
 template <typename T>
-static const void *sweep_kernel_ptr(int variant, int apw, bool tab) {
+static const void *sweep_kernel_ptr(int variant, int apw, bool tab, bool lean) {
   if constexpr (sizeof(T) == 8) {
-    if (tab) return kernel_for_variant<T, true>(variant, apw);
+    if (tab) return kernel_for_variant<T, true, false>(variant, apw);
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (lean) return kernel_for_variant<T, false, true>(variant, apw);
   }
   (void)tab;
-  return kernel_for_variant<T, false>(variant, apw);
+  (void)lean;
+  return kernel_for_variant<T, false, false>(variant, apw);
 }
 
 template <typename T>
 int sweep_blocks_per_sm(int variant, int warps, int apw) {
-  const void *k = sweep_kernel_ptr<T>(variant, apw, false);
+  const void *k = sweep_kernel_ptr<T>(variant, apw, false, false);
   const size_t smem = sweep_smem_bytes<T>(variant, warps, apw);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
@@ -1010,7 +1029,8 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   }
   cudaError_t e = cudaMemsetAsync(a.ctrl, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr);
+  const bool lean = !a.source && a.psi == nullptr && a.corr == nullptr;
+  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr, lean);
   const size_t smem = sweep_smem_bytes<T>(variant, a.g.warps, a.g.apw);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
