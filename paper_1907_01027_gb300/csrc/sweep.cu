@@ -378,9 +378,9 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 #endif
 
 // TAB: the element-solve coefficients come from the FP64 tables (per material and direction class; FP64
-// instances only), else they are formed in the kernel from sigma_t h.  LEAN: the homogeneous, non-storing sweep
-// of the GMRES iterations (no source, inflow data, stored unknowns or correlation), compiled without the
-// per-step tests for them (FP32 instances).
+// instances only), else they are formed in the kernel from sigma_t h.  LEAN: a non-storing sweep without inflow
+// data, angle-dependent source or correlation (the GMRES iterations; the residual sweeps of problems with vacuum
+// inflow and isotropic source), compiled without the per-step tests for them (FP32 and float-float instances).
 template <typename T, int VAR, int APW, bool TAB, bool LEAN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr bool P0 = VAR == kP0;         // P0-DG: the LMDG row-0 solve without slopes
@@ -976,13 +976,19 @@ static const void *kernel_for_variant(int variant, int apw) {
   }
 }
 
-// coefficient tables exist for the FP64 and float-float sweeps; lean instances for FP32
+// coefficient tables exist for the FP64 and float-float sweeps; lean instances for FP32 and float-float
 template <typename T>
 static const void *sweep_kernel_ptr(int variant, int apw, bool tab, bool lean) {
+  constexpr bool kLean = !std::is_same<T, double>::value;
   if constexpr (sizeof(T) == 8) {
-    if (tab) return kernel_for_variant<T, true, false>(variant, apw);
+    if (tab) {
+      if constexpr (kLean) {
+        if (lean) return kernel_for_variant<T, true, true>(variant, apw);
+      }
+      return kernel_for_variant<T, true, false>(variant, apw);
+    }
   }
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (kLean) {
     if (lean) return kernel_for_variant<T, false, true>(variant, apw);
   }
   (void)tab;
@@ -1029,7 +1035,9 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   }
   cudaError_t e = cudaMemsetAsync(a.ctrl, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  const bool lean = !a.source && a.psi == nullptr && a.corr == nullptr;
+  // lean: nothing a lean instance leaves out is needed -- a source sweep without inflow data or angle-dependent
+  // source (its source enters through prep_kernel's cell data) runs the same per-step code as a homogeneous one
+  const bool lean = !(a.source && (a.pd.alpha != nullptr || a.q_per_angle)) && a.psi == nullptr && a.corr == nullptr;
   const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr, lean);
   const size_t smem = sweep_smem_bytes<T>(variant, a.g.warps, a.g.apw);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -94,3 +94,32 @@ def test_mixed_adjoint_with_f32x2_residuals():
     assert abs(J - J0) <= 1e-9 * abs(J0)
     assert rel(dss, a0) < 1e-5 and rel(dsa, b0) < 1e-5 and rel(dq, c0) < 1e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", ["std", "lm", "rlm", "p0"])
+@pytest.mark.parametrize("n,N,eps,seed", [(5, 4, 1.0, 31), (70, 8, 0.3, 32)])
+def test_source_sweep_vacuum_isotropic(variant, n, N, eps, seed):
+    """Vacuum inflow and an isotropic source: the residual sweeps of such problems (the benchmark's) run the lean
+    instances in FP32 and float-float."""
+    from paper_1907_01027_gb300 import Context, SWEEP_F32X2, SWEEP_FP32, SWEEP_SOURCE
+    p = random_problem(n, N, eps, seed, alpha=False, q_per_angle=False)
+    so = SweepOracle(p)
+    ctx = Context(p, variant)
+    x = np.random.default_rng(seed + 100).standard_normal((p.nx, 4))
+    ref = so.K(variant, x) - _bprime(so, variant)
+    assert rel(ctx.sweep(x, flags=SWEEP_F32X2 | SWEEP_SOURCE), ref) < TOL_F2
+    assert rel(ctx.sweep(x, flags=SWEEP_SOURCE), ref) < 1e-12
+    assert rel(ctx.sweep(x, flags=SWEEP_FP32 | SWEEP_SOURCE), ref) < 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", ["std", "lm", "rlm"])
+def test_mixed_solve_vacuum_isotropic(variant):
+    from paper_1907_01027_gb300 import Context, FP32, RESID_F32X2
+    p = random_problem(16, 4, 1.0, 33, alpha=False, q_per_angle=False)
+    ref = SweepOracle(p).solve(variant, direct=True)
+    ctx = Context(p, variant, precision=FP32, resid=RESID_F32X2, tol=1e-12, max_iters=20000)
+    _, phi, st, rc = ctx.solve()
+    assert rc == 0 and st["sweeps_f32x2"] >= 1, st
+    assert rel(phi, ref["phi"]) < 1e-8
+    ctx.close()
