@@ -54,7 +54,7 @@ void harvest(lmdg_ctx *c, bool wait) {
 // Float-float copies of the problem data and coefficient tables, made from the FP64 ones on the first
 // float-float sweep.
 int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
-  if (c->d2.ox) return 0;
+  if (c->f2_ready) return 0;
   const size_t na = c->nang, nx = c->nx;
   const size_t nq = c->q_layout == 2 ? na * nx * 4 : nx * 4;
   const size_t nal = c->has_alpha ? na * 4 * (size_t)c->n * 2 : 0;
@@ -63,11 +63,16 @@ int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
       {c->d64.ox, &c->d2.ox, na}, {c->d64.oy, &c->d2.oy, na}, {c->d64.w, &c->d2.w, na},
       {c->d64.sigt, &c->d2.sigt, nx}, {c->d64.sse, &c->d2.sse, nx}, {c->d64.q, &c->d2.q, nq},
       {c->d64.alpha, &c->d2.alpha, nal}, {c->p1ra64, &c->p1ra2, 2 * nx}, {c->coef, &c->coef2, ntab}};
+  // a failed allocation leaves the arrays made so far in place (freed by lmdg_destroy) for the next attempt
   for (auto &it : items) {
     if (it.n == 0 || it.src == nullptr) continue;
-    if (cudaMalloc(it.dst, sizeof(f2) * it.n) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (*it.dst == nullptr && cudaMalloc(it.dst, sizeof(f2) * it.n) != cudaSuccess) {
+      *it.dst = nullptr;
+      return LMDG_ERR_NOMEM;
+    }
     CK(convert_to_f2(it.src, *it.dst, it.n, s));
   }
+  c->f2_ready = true;
   return 0;
 }
 

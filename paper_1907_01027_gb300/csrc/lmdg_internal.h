@@ -121,6 +121,7 @@ struct lmdg_ctx {
   lmdg::ProblemData<double> d64;
   lmdg::ProblemData<float> d32;
   lmdg::ProblemData<lmdg::f2> d2;          // float-float copies (residual sweeps of the mixed-precision solve)
+  bool f2_ready = false;                   // d2, p1ra2 and coef2 hold the converted data
   double *p1ra64 = nullptr;                // [nx][2]
   float *p1ra32 = nullptr;
   lmdg::f2 *p1ra2 = nullptr;
