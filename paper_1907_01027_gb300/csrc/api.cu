@@ -26,9 +26,14 @@ int quadrant(double ox, double oy) { return oy > 0 ? (ox > 0 ? 0 : 1) : (ox < 0 
 
 template <typename T>
 int upload(T **dst, const std::vector<double> &src) {
-  std::vector<T> tmp(src.begin(), src.end());
-  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, tmp.size())) != cudaSuccess) return LMDG_ERR_NOMEM;
-  if (!tmp.empty()) CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size())) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (src.empty()) return 0;
+  if constexpr (std::is_same<T, double>::value) {
+    CK(cudaMemcpy(*dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<T> tmp(src.begin(), src.end());
+    CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  }
   return 0;
 }
 
@@ -527,14 +532,13 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     qm[3] += w[l] * ox[l]; qm[4] += w[l] * oy[l];
   }
   // diagonal of B11: eps sigma_a h^2 D_r + outflow face terms (Jacobi right preconditioner)
-  std::vector<double> bd(nx * 3);
+  std::vector<double> bdinv(nx * 3);
   const double fx[3] = {1.0, 1.0 / 3.0, 1.0 / 3.0}, fy[3] = {1.0 / 3.0, 1.0, 1.0 / 3.0};
   for (size_t K = 0; K < nx; ++K)
     for (int r = 0; r < 3; ++r)
-      bd[3 * K + r] = eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r];
+      bdinv[3 * K + r] =   // the preconditioner multiplies by the reciprocal
+          1.0 / (eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r]);
 
-  std::vector<double> bdinv(bd.size());
-  for (size_t k = 0; k < bd.size(); ++k) bdinv[k] = 1.0 / bd[k];   // the preconditioner multiplies
 
   // opposite direction of every sorted direction (central symmetry, needed by the adjoint)
   std::vector<int> rev(na, 0);
@@ -609,12 +613,18 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   {
     std::vector<double> sh(nx);
     for (size_t K = 0; K < nx; ++K) sh[K] = sigt[K] * h;
-    std::vector<double> uniq(sh);
+    // distinct values, sorted: runs of equal neighbours (piecewise-constant media) are skipped before the sort,
+    // and a cell equal to its predecessor takes its index without a search
+    std::vector<double> uniq;
+    for (size_t K = 0; K < nx; ++K)
+      if (K == 0 || sh[K] != sh[K - 1]) uniq.push_back(sh[K]);
     std::sort(uniq.begin(), uniq.end());
     uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
     std::vector<int> matv(nx);
     for (size_t K = 0; K < nx; ++K)
-      matv[K] = (int)(std::lower_bound(uniq.begin(), uniq.end(), sh[K]) - uniq.begin());
+      matv[K] = (K > 0 && sh[K] == sh[K - 1])
+                    ? matv[K - 1]
+                    : (int)(std::lower_bound(uniq.begin(), uniq.end(), sh[K]) - uniq.begin());
     std::vector<double> cab;
     std::vector<int> clsv(na);
     for (int k = 0; k < na; ++k) {
