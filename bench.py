@@ -339,15 +339,22 @@ def run_gpu(args, rank, ws, dist):
 
     # end to end through the public API with host buffers: setup from host arrays, solve, phi back to host
     e2e_ms, e2e_upd = 0.0, 0
+    part_ms = {"setup": 0.0, "solve": 0.0, "destroy": 0.0}
     h2d = d2h = 0
     for k in range(max(1, args.steps)):
         for v in VARIANTS:
             t0 = time.perf_counter()
             ctx = Context(p, v, precision=FP32, resid=RESID_F32X2, tol=1e-8, device=local)
+            t1 = time.perf_counter()
             _, phi, st, rc = ctx.solve(want_x=False, want_phi=True, device=False)
+            t2 = time.perf_counter()
             ctx.close()
             torch.cuda.synchronize()
-            e2e_ms += 1e3 * (time.perf_counter() - t0)
+            t3 = time.perf_counter()
+            e2e_ms += 1e3 * (t3 - t0)
+            part_ms["setup"] += 1e3 * (t1 - t0)
+            part_ms["solve"] += 1e3 * (t2 - t1)
+            part_ms["destroy"] += 1e3 * (t3 - t2)
             e2e_upd += (st["sweeps_fp32"] + st["sweeps_fp64"] + st["sweeps_f32x2"]) * upd
             if k == 0:
                 h2d += 8 * (3 * p.nang + 2 * p.nx + 4 * p.nx)
@@ -355,7 +362,8 @@ def run_gpu(args, rank, ws, dist):
     out["e2e"] = {"value": e2e_upd / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": d2h,
                   "what": "lmdg_setup from host arrays + lmdg_solve (LMDG_HOST_PTRS, phi to host) + destroy, "
-                          "three schemes per step"}
+                          "three schemes per step",
+                  "ms_per_step": {k: t / max(1, args.steps) for k, t in part_ms.items()}}
 
     if rank == 0 and ws == 1 and not args.skip_cpu:
         v, cores, desc, dt = cpu_oracle_sample(p, per_variant=16)
