@@ -24,17 +24,22 @@ namespace {
 
 int quadrant(double ox, double oy) { return oy > 0 ? (ox > 0 ? 0 : 1) : (ox < 0 ? 2 : 3); }
 
+// n host doubles to a new device array of T (converted on the host when T is not double)
 template <typename T>
-int upload(T **dst, const std::vector<double> &src) {
-  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size())) != cudaSuccess) return LMDG_ERR_NOMEM;
-  if (src.empty()) return 0;
+int upload(T **dst, const double *src, size_t n) {
+  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, n)) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (n == 0) return 0;
   if constexpr (std::is_same<T, double>::value) {
-    CK(cudaMemcpy(*dst, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(*dst, src, sizeof(double) * n, cudaMemcpyHostToDevice));
   } else {
-    std::vector<T> tmp(src.begin(), src.end());
-    CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+    std::vector<T> tmp(src, src + n);
+    CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
   }
   return 0;
+}
+template <typename T>
+int upload(T **dst, const std::vector<double> &src) {
+  return upload(dst, src.data(), src.size());
 }
 
 template <typename T>
@@ -464,19 +469,21 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   std::copy(perm.begin(), perm.end(), c->perm_h);
   std::vector<double> ox(na), oy(na), w(na);
   for (int k = 0; k < na; ++k) { ox[k] = quad->ox[perm[k]]; oy[k] = quad->oy[perm[k]]; w[k] = quad->w[perm[k]]; }
-  std::vector<double> sigt(nx), sse(nx), sa(sigma_a, sigma_a + nx);
+  std::vector<double> sigt(nx), sse(nx);
   for (size_t K = 0; K < nx; ++K) { sigt[K] = sigma_s[K] / eps + eps * sigma_a[K]; sse[K] = sigma_s[K] / eps; }
   std::vector<double> qv;
   if (q_layout == 0) {
     qv.assign(nx * 4, 0.0);
     for (size_t K = 0; K < nx; ++K) qv[4 * K] = q[K];
   } else if (q_layout == 1) {
-    qv.assign(q, q + nx * 4);
+    // the caller's array is uploaded as it is (qsrc below)
   } else {
     qv.resize((size_t)na * nx * 4);
     for (int k = 0; k < na; ++k)
       std::memcpy(&qv[(size_t)k * nx * 4], q + (size_t)perm[k] * nx * 4, sizeof(double) * nx * 4);
   }
+  const double *qsrc = q_layout == 1 ? q : qv.data();
+  const size_t qn = q_layout == 1 ? nx * 4 : qv.size();
   std::vector<double> av;
   if (alpha) {
     const size_t per = (size_t)4 * n * 2;
@@ -560,11 +567,11 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (cudaMemcpy(c->perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LMDG_ERR_CUDA);
   if ((e = upload(&c->d64.ox, ox)) || (e = upload(&c->d64.oy, oy)) || (e = upload(&c->d64.w, w)) ||
-      (e = upload(&c->d64.sigt, sigt)) || (e = upload(&c->d64.sse, sse)) || (e = upload(&c->d64.q, qv)) ||
+      (e = upload(&c->d64.sigt, sigt)) || (e = upload(&c->d64.sse, sse)) || (e = upload(&c->d64.q, qsrc, qn)) ||
       (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
-      (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qv)) ||
+      (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qsrc, qn)) ||
       (e = upload(&c->p1ra64, p1ra)) || (e = upload(&c->p1ra32, p1ra)) || (e = upload(&c->sq1, sq1)) ||
-      (e = upload(&c->b11dinv, bdinv)) || (e = upload(&c->sigma_a, sa)) || (e = upload(&c->qmom, qm)))
+      (e = upload(&c->b11dinv, bdinv)) || (e = upload(&c->sigma_a, sigma_a, nx)) || (e = upload(&c->qmom, qm)))
     return fail(e);
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
