@@ -139,7 +139,7 @@ int lmdg_default_options(lmdg_options *opt);
  *                      coordinate.  Only inflow faces are read.  The reconstruction of RLMDG uses a0 as the
  *                      face-midpoint value of alpha (Section 3.3.1).
  *   eps              : scaling parameter epsilon > 0 of eq-main.
- *   variant          : LMDG_STD, LMDG_LM or LMDG_RLM.
+ *   variant          : LMDG_STD, LMDG_LM, LMDG_RLM or LMDG_P0.
  *   opt              : NULL for defaults.
  * Device memory: O(n_Omega * n^2) for the angular-flux store, O(n^2) for the rest. */
 int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad,
@@ -153,12 +153,15 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
  *   LMDG_LM  : K [X0; X1] of eq-lmdg-reducemat, evaluated as in eq-nonrec-block; x = (X0, X1) per cell;
  *              b = the right-hand side of eq-lmdg-reducemat minus K [0; z], z = B11^-1 Sigma Q1.
  *   LMDG_RLM : the reduced RLMDG operator of Section 3.3.2 with the second block row
- *              G' = Sigma Ltilde10 + B11 P1 R (the printed row does not close; see the design notes);
+ *              G' = Sigma Ltilde10 + B11 P1 R (with X1 = (B11^-1 Sigma Ltilde10 + P1 R) Psi0 the printed row
+ *              Sigma Ltilde10 leaves a B11 P1 R Psi0 term unclosed);
  *              b = its right-hand side minus K [0; z], z = B11^-1 Sigma Qtilde1.
  * With LMDG_SWEEP_SOURCE the call returns y = K x - b, so that the solution of lmdg_solve zeroes it (for the
  * low-memory variants this is the paper's system written for the shifted unknown X1 - z, i.e. GMRES started
  * from X1 = z).  LMDG_SWEEP_STORE keeps this sweep's angular unknowns: psi [n_Omega][n*n][4] for LMDG_STD,
- * psi0 [n_Omega][n*n] for the low-memory variants.  Asynchronous on stream for device pointers. */
+ * psi0 [n_Omega][n*n] for the low-memory variants.  LMDG_SWEEP_FP32 / LMDG_SWEEP_F32X2 run the sweep in float /
+ * float-float (x and y stay double); LMDG_SWEEP_F32X2 with LMDG_SWEEP_FP32 or LMDG_SWEEP_STORE returns
+ * LMDG_ERR_ARG.  Asynchronous on stream for device pointers. */
 int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
 
 /* Solve the reduced system with restarted GMRES (right-preconditioned, see lmdg_options.precond), then run
