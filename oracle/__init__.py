@@ -14,6 +14,8 @@ Two independent implementations of what the method computes:
   Sigma, B11 and R applied matrix-free, transport sweeps as block lower-triangular solves in upwind order,
   the reduced systems eq-sndg-phi / eq-lmdg-reducemat / eq-rlmdg-reducemat solved by a library Krylov
   method, and the recovery steps.  Any mesh size.
+* :mod:`oracle.dsa` -- the diffusion correction of the cell averages, a right preconditioner for GMRES on the
+  reduced systems (not from the paper, which leaves preconditioners to future work).
 * :mod:`oracle.slab1d` -- the slab-geometry versions of the schemes (Section 4.1), assembled as trial/test
   restrictions of the 1D P1 form and solved directly: a cross-check of the scheme readings against the
   paper's printed 1D errors.

@@ -448,7 +448,9 @@ class SweepOracle:
         ``X`` (reduced unknowns [n_x][4]) and ``iters``.
 
         ``precond='jacobi'`` (default for the low-memory variants) right-preconditions GMRES by
-        diag(I, diag(B11))^-1, which leaves the residual of the original system unchanged."""
+        diag(I, diag(B11))^-1, which leaves the residual of the original system unchanged; ``precond='dsa'``
+        adds the diffusion correction of the cell averages (:mod:`oracle.dsa`) to it (to the identity for the
+        standard scheme and P0-DG)."""
         if precond is None:
             precond = "none" if variant in ("std", "p0") else "jacobi"
         b = self.rhs(variant).ravel()
@@ -459,15 +461,22 @@ class SweepOracle:
         if direct:
             X = np.linalg.solve(self.dense_K(variant), b)
         else:
-            if precond == "jacobi":
-                D = np.ones((self.nx, 4))
+            D = np.ones((self.nx, 4))
+            if variant not in ("std", "p0") and precond in ("jacobi", "dsa"):
                 D[:, 1:] = self.B11mat().diagonal().reshape(self.nx, 3)
+            if precond == "dsa":
+                from oracle.dsa import DiffusionCorrection
+                corr = DiffusionCorrection(self.p)
+                Minv = lambda v: corr(v) / D.ravel()
+            elif precond == "jacobi":
                 Minv = lambda v: v / D.ravel()
             else:
                 Minv = lambda v: v
             op = spla.LinearOperator((n4, n4), matvec=lambda v: self.K(variant, Minv(v)).ravel(),
                                      dtype=np.float64)
             cnt = [0]
+            if x0 is not None and precond == "dsa":
+                raise ValueError("an initial guess is not supported with the diffusion correction")
             y0 = None if x0 is None else x0.ravel() * (1.0 if precond != "jacobi" else D.ravel())
             Y, ierr = spla.gmres(op, b, x0=y0, rtol=tol, atol=0.0, restart=restart, maxiter=maxiter,
                                  callback=lambda r: cnt.__setitem__(0, cnt[0] + 1), callback_type="pr_norm")
