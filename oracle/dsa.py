@@ -43,15 +43,68 @@ def diffusion_matrix(p):
     return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n * n, n * n))
 
 
-class DiffusionCorrection:
-    """v -> v with v[:, 0] += D_a^-1 (sigma_s / eps) v[:, 0] (sparse LU of the finite-volume matrix)."""
+class SmoothedAggregation:
+    """One V-cycle of smoothed-aggregation multigrid for the finite-volume matrix: the approximate D_a^-1 of
+    a device implementation, written out step by step (Vanek, Mandel and Brezina 1996, on the structured mesh).
 
-    def __init__(self, p):
-        self.lu = spla.splu(diffusion_matrix(p))
+    Levels: 2 x 2 cell aggregates (n even) give the tentative prolongation P0 (piecewise constant); the
+    prolongation P = (I - omega_p D^-1 A) P0 is P0 smoothed by one damped-Jacobi step with omega_p = 2/3; the
+    coarse matrix is the Galerkin product P^T A P.  Down to n <= 4 (or an odd n), where a sparse LU solves.  The
+    cycle: nu damped-Jacobi steps (omega = 0.8) on the zero guess, the coarse correction of the residual, nu more
+    steps."""
+
+    def __init__(self, A, n, nu=2, omega=0.8, omega_p=2.0 / 3.0):
+        self.levels = []
+        A = sp.csr_matrix(A)
+        while n > 4 and n % 2 == 0:
+            m = n // 2
+            J, I = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+            P0 = sp.csr_matrix((np.ones(n * n), ((J * n + I).ravel(), ((J // 2) * m + I // 2).ravel())),
+                               shape=(n * n, m * m))
+            dinv = 1.0 / A.diagonal()
+            P = (P0 - omega_p * (sp.diags(dinv) @ (A @ P0))).tocsr()
+            self.levels.append((A, P, dinv))
+            A, n = (P.T @ A @ P).tocsr(), m
+        self.coarse = spla.splu(A.tocsc())
+        self.nu, self.omega = nu, omega
+
+    def vcycle(self, b, level=0):
+        if level == len(self.levels):
+            return self.coarse.solve(b)
+        A, P, dinv = self.levels[level]
+        x = np.zeros_like(b)
+        for _ in range(self.nu):
+            x = x + self.omega * dinv * (b - A @ x)
+        x = x + P @ self.vcycle(P.T @ (b - A @ x), level + 1)
+        for _ in range(self.nu):
+            x = x + self.omega * dinv * (b - A @ x)
+        return x
+
+
+class DiffusionCorrection:
+    """v -> v with v[:, 0] += D_a^-1 (sigma_s / eps) v[:, 0]: a sparse LU of the finite-volume matrix
+    (``cycles=None``) or that many smoothed-aggregation V-cycles from zero."""
+
+    def __init__(self, p, cycles=None):
+        A = diffusion_matrix(p)
+        self.cycles = cycles
+        if cycles is None:
+            self.lu = spla.splu(A)
+        else:
+            self.A = A.tocsr()
+            self.mg = SmoothedAggregation(A, p.n)
         self.src = np.asarray(p.sigma_s, dtype=float) / p.eps * p.h * p.h
         self.nx = p.nx
 
+    def solve(self, r):
+        if self.cycles is None:
+            return self.lu.solve(r)
+        d = np.zeros_like(r)
+        for _ in range(self.cycles):
+            d = d + self.mg.vcycle(r - self.A @ d)
+        return d
+
     def __call__(self, v):
         w = np.array(v, dtype=float).reshape(self.nx, 4)
-        w[:, 0] += self.lu.solve(self.src * w[:, 0])
+        w[:, 0] += self.solve(self.src * w[:, 0])
         return w.ravel()

@@ -443,14 +443,15 @@ class SweepOracle:
             cols.append(self.K(variant, e).ravel())
         return np.array(cols).T
 
-    def solve(self, variant, tol=1e-12, restart=30, maxiter=20000, direct=None, x0=None, precond=None):
+    def solve(self, variant, tol=1e-12, restart=30, maxiter=20000, direct=None, x0=None, precond=None,
+              dsa_cycles=None):
         """Solve the reduced system and recover the solution.  Returns a dict like ``dense.solve`` plus
         ``X`` (reduced unknowns [n_x][4]) and ``iters``.
 
         ``precond='jacobi'`` (default for the low-memory variants) right-preconditions GMRES by
         diag(I, diag(B11))^-1, which leaves the residual of the original system unchanged; ``precond='dsa'``
         adds the diffusion correction of the cell averages (:mod:`oracle.dsa`) to it (to the identity for the
-        standard scheme and P0-DG)."""
+        standard scheme and P0-DG), solved exactly or (``dsa_cycles``) by that many multigrid V-cycles."""
         if precond is None:
             precond = "none" if variant in ("std", "p0") else "jacobi"
         b = self.rhs(variant).ravel()
@@ -466,7 +467,7 @@ class SweepOracle:
                 D[:, 1:] = self.B11mat().diagonal().reshape(self.nx, 3)
             if precond == "dsa":
                 from oracle.dsa import DiffusionCorrection
-                corr = DiffusionCorrection(self.p)
+                corr = DiffusionCorrection(self.p, cycles=dsa_cycles)
                 Minv = lambda v: corr(v) / D.ravel()
             elif precond == "jacobi":
                 Minv = lambda v: v / D.ravel()

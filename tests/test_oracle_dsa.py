@@ -52,3 +52,31 @@ def test_preconditioned_solve(variant):
         assert dsa["iters"] <= 0.8 * base["iters"], (dsa["iters"], base["iters"])
     else:
         assert dsa["iters"] <= base["iters"] + 2, (dsa["iters"], base["iters"])
+
+
+def test_multigrid_cycle_contracts():
+    """Smoothed-aggregation V-cycles on the benchmark's medium at 64 x 64 cells: the error of the diffusion
+    solve falls at least 5x per cycle (against the sparse LU solution)."""
+    import scipy.sparse.linalg as spla
+    from oracle.dsa import SmoothedAggregation
+    p = config4(eps=1.0, n=64, patch=1, N=4)
+    A = diffusion_matrix(p).tocsr()
+    mg = SmoothedAggregation(A, p.n)
+    assert len(mg.levels) == 4                                   # 64 -> 32 -> 16 -> 8 -> 4
+    b = np.random.default_rng(1).standard_normal(p.nx)
+    exact = spla.spsolve(A.tocsc(), b)
+    x = np.zeros_like(b)
+    errs = []
+    for _ in range(4):
+        x = x + mg.vcycle(b - A @ x)
+        errs.append(np.linalg.norm(x - exact) / np.linalg.norm(exact))
+    assert errs[0] < 0.2 and all(e1 < 0.2 * e0 for e0, e1 in zip(errs, errs[1:])), errs
+
+
+def test_one_cycle_correction_as_good_as_exact():
+    p = config4(eps=1.0, n=16, patch=1, N=4)
+    so = SweepOracle(p)
+    exact = so.solve("std", tol=1e-12, direct=False, precond="dsa")
+    one = so.solve("std", tol=1e-12, direct=False, precond="dsa", dsa_cycles=1)
+    assert rel(one["phi"], exact["phi"]) < 1e-8
+    assert one["iters"] <= exact["iters"] + 1, (one["iters"], exact["iters"])
