@@ -131,6 +131,33 @@ def peaks():
         return {}
 
 
+def host_cpu():
+    """(logical cores, model string) of this host."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "Model Name"):
+                model = v.strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                k, _, v = line.partition(":")
+                if k.strip() == "Model name":
+                    model = v.strip()
+                    break
+        except Exception:
+            pass
+    if model is None:
+        import platform
+        model = platform.machine() or "unknown"
+    return os.cpu_count() or 1, model
+
+
 def cpu_oracle_sample(p, per_variant=16, threads=None):
     """Oracle transport sweeps (its per-direction upwind solves) on a subset of the workload's directions:
     returns (cell-angle updates/s, cores, description)."""
@@ -163,12 +190,13 @@ def run_reference(args, rank, ws):
         return 0
     from workloads.problems import config4
     p = config4(eps=1.0)
+    nproc, model = host_cpu()
     for _ in range(args.warmup):
-        cpu_oracle_sample(p, per_variant=2)
+        cpu_oracle_sample(p, per_variant=2, threads=nproc)
     vals, times = [], []
     desc = cores = None
     for _ in range(args.steps):
-        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=4)
+        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=4, threads=nproc)
         vals.append(v)
         times.append(dt)
     value = len(vals) / sum(1.0 / v for v in vals)
@@ -176,7 +204,8 @@ def run_reference(args, rank, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "nproc": nproc, "cpu": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -252,7 +281,7 @@ def run_gpu(args, rank, ws, dist):
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 512x512 profiling "
                                   "case, per scheme, scaled by the cell count and averaged over the timed "
-                                  "launches (profiles/sweep_kernels_512x512_S16.md)",
+                                  "launches",
                 "peak_source": "FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                 "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n,
                 "flops_per_update": FLOPS_PER_UPDATE,
@@ -366,9 +395,12 @@ def run_gpu(args, rank, ws, dist):
                   "ms_per_step": {k: t / max(1, args.steps) for k, t in part_ms.items()}}
 
     if rank == 0 and ws == 1 and not args.skip_cpu:
-        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=16)
+        nproc, model = host_cpu()
+        v, cores, desc, dt = cpu_oracle_sample(p, per_variant=16, threads=nproc)
+        v1, _, desc1, dt1 = cpu_oracle_sample(p, per_variant=2, threads=1)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-                               "seconds": dt}
+                               "seconds": dt, "nproc": nproc, "cpu": model,
+                               "one_thread": {"value": v1, "sample": desc1, "seconds": dt1}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     for c in ctxs.values():

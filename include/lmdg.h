@@ -209,8 +209,9 @@ int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *i
  *   variant          : LMDG_STD, LMDG_LM or LMDG_RLM.
  *   n, h             : n x n cells of side h.
  *   n_omega, ox, oy, w : DEVICE arrays [n_omega] of directions and weights, grouped by quadrant in the order
- *                      (+,+), (-,+), (-,-), (+,-) with n_omega/4 directions each (not checked: the arrays
- *                      stay on the device); n_omega a multiple of 4, at most 1024.
+ *                      (+,+), (-,+), (-,-), (+,-) with n_omega/4 directions each; n_omega a multiple of 4, at
+ *                      most 1024.  The grouping is checked on the device before the sweep: a direction whose
+ *                      signs do not match its quadrant slot, or that lies on an axis, returns LMDG_ERR_QUAD.
  *   sigma_t          : DEVICE [n*n] sigma_s/eps + eps sigma_a;  sigma_s_over_eps : DEVICE [n*n] sigma_s/eps.
  *   x, y             : DEVICE [n*n][4] doubles, 16-byte aligned (x: input, y: output, distinct).
  *   spin_limit       : polls of a readiness flag before giving up with LMDG_ERR_TIMEOUT.

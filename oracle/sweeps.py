@@ -79,7 +79,7 @@ class SweepOracle:
         self.sigt = np.ascontiguousarray(p.sigma_s / p.eps + p.eps * p.sigma_a, dtype=np.float64)
         self.sse = p.sigma_s / p.eps
         self.mass = elem_tables(p.h)["mass"]
-        self.threads = threads or min(16, os.cpu_count() or 1)
+        self.threads = threads or (os.cpu_count() or 1)
         self.lib = _load()
         self.cg_iters = 0
 

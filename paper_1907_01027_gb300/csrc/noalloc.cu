@@ -37,6 +37,19 @@ __global__ void identity_kernel(int *perm, int count) {
   if (k < count) perm[k] = k;
 }
 
+// bad[0] = number of directions whose signs do not match their quadrant slot (slots of n_omega / 4 directions
+// in the order (+,+), (-,+), (-,-), (+,-)) or that lie on an axis
+__global__ void quadrant_check_kernel(int nang, const double *__restrict__ ox, const double *__restrict__ oy,
+                                      unsigned *__restrict__ bad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nang) return;
+  const int quad = k / (nang / 4);
+  const double a = ox[k], b = oy[k];
+  const bool ok = (quad == 0 && a > 0 && b > 0) || (quad == 1 && a < 0 && b > 0) ||
+                  (quad == 2 && a < 0 && b < 0) || (quad == 3 && a > 0 && b < 0);
+  if (!ok) atomicAdd(bad, 1u);
+}
+
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Groups of at most 8 warps x kMaxA directions, every group non-empty (a fixed shape: no occupancy query).
@@ -88,10 +101,11 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   const SweepGeom g = geom_for(n, nq);
   const size_t nx = (size_t)n * n;
   const int NR = variant == LMDG_RLM ? 6 : 4;
-  // scratch layout: [perm (kMaxDirections ints)] [quadrature moments] [control words] [cell inputs] [partials]
-  // [strip traces]
+  // scratch layout: [perm (kMaxDirections ints)] [quadrature moments] [direction check word] [control words]
+  // [cell inputs] [partials] [strip traces]
   const size_t off_qm = align256(sizeof(int) * kMaxDirections);
-  const size_t off_ctrl = off_qm + align256(sizeof(double) * 5);
+  const size_t off_chk = off_qm + align256(sizeof(double) * 5);
+  const size_t off_ctrl = off_chk + align256(sizeof(unsigned));
   const size_t off_cell = off_ctrl + align256(sizeof(unsigned) * (2 + (size_t)g.units()));
   const size_t off_cellh = off_cell + align256(sizeof(double) * 4 * nx);
   const size_t off_part = off_cellh + align256(sizeof(double) * nx);
@@ -100,6 +114,19 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   if (need > kScratchBytes) return LMDG_ERR_ARG;   // problem too large for the fixed scratch
   unsigned char *base = nullptr;
   if (int e = scratch_for_current_device(&base, s)) return e;
+  // the directions must come grouped by quadrant: checked on the device before the sweep (they stay there)
+  {
+    unsigned *chk = reinterpret_cast<unsigned *>(base + off_chk);
+    unsigned bad = 0;
+    if (cudaMemsetAsync(chk, 0, sizeof(unsigned), s) != cudaSuccess) return LMDG_ERR_CUDA;
+    add_launches(1);
+    quadrant_check_kernel<<<(n_omega + 255) / 256, 256, 0, s>>>(n_omega, ox, oy, chk);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&bad, chk, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return LMDG_ERR_CUDA;
+    if (bad) return LMDG_ERR_QUAD;
+  }
 
   SweepArgs<double> a{};
   a.n = n; a.nq = nq; a.nang = n_omega; a.nx = (int)nx;

@@ -238,10 +238,18 @@ __device__ __forceinline__ f2 ld_relaxed_t(const f2 *p) {
   asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return f2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
 }
-template <typename T> __device__ __forceinline__ void st_trace(T *p, T v) { *p = v; }
-template <> __device__ __forceinline__ void st_trace<f2>(f2 *p, f2 v) {
-  *reinterpret_cast<unsigned long long *>(p) =
+// Trace stores are relaxed at GPU scope, like the polling loads, so the data-carried readiness protocol is
+// race-free in the PTX memory model (a weak store paired with a relaxed load would be a data race there).
+__device__ __forceinline__ void st_trace(float *p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+__device__ __forceinline__ void st_trace(double *p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+__device__ __forceinline__ void st_trace(f2 *p, f2 v) {
+  const unsigned long long b =
       ((unsigned long long)__float_as_uint(v.lo) << 32) | (unsigned long long)__float_as_uint(v.hi);
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b));
 }
 
 // Sign flip by the bit pattern (an integer op instead of an FP64 multiply): m = 0 keeps v, m = 0x80000000 negates.

@@ -15,7 +15,7 @@ VARIANTS = {"std": STD, "lm": LM, "rlm": RLM, "p0": P0}
 FP64, FP32, FP32_BF16STORE = 0, 1, 2
 SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS, SWEEP_F32X2 = 1, 2, 4, 8, 16
 RESID_FP64, RESID_F32X2 = 0, 1
-ERR_TIMEOUT, ERR_NOTCONV = -6, -5
+ERR_TIMEOUT, ERR_NOTCONV, ERR_BREAKDOWN = -6, -5, -7
 
 
 class LmdgError(RuntimeError):
@@ -159,8 +159,10 @@ class Context:
         self._check(rc, "lmdg_sweep")
         return y
 
-    def solve(self, x0=None, want_x=True, want_phi=True, device=False):
-        """lmdg_solve.  Returns (x, phi, stats dict, status)."""
+    def solve(self, x0=None, want_x=True, want_phi=True, device=False, allow_stall=False):
+        """lmdg_solve.  Returns (x, phi, stats dict, status).  LMDG_ERR_NOTCONV returns normally (outputs written);
+        with ``allow_stall`` so does LMDG_ERR_BREAKDOWN from a residual that stopped decreasing (a solve driven
+        below what the arithmetic can reach)."""
         st = Stats()
         if device:
             import torch
@@ -176,7 +178,7 @@ class Context:
             rc = self.lib.lmdg_solve(self.h, None if x0a is None else x0a.ctypes.data,
                                      None if x is None else x.ctypes.data, None if phi is None else phi.ctypes.data,
                                      ctypes.byref(st), HOST_PTRS, None)
-        self._check(rc, "lmdg_solve", allow=(ERR_NOTCONV,))
+        self._check(rc, "lmdg_solve", allow=(ERR_NOTCONV, ERR_BREAKDOWN) if allow_stall else (ERR_NOTCONV,))
         return x, phi, st.as_dict(), rc
 
     def get_psi(self):

@@ -1,0 +1,78 @@
+"""Adjoint gradients at the adjoint workload's full size (256 x 256 cells, S8, sigma_s = 1 + 8 Gaussian bumps,
+sigma_a = 0.1, detector x > 0.9) against central differences on the 32 seeded cells (default_rng(1908)).
+
+A plain difference of two solves loses the change of J to cancellation here (one cell's perturbation moves J by
+about 1e-8 of itself), so each side is a difference solve: with A(p) psi = Q the perturbed solution is
+psi + dpsi with A(p + d) dpsi = -(A(p + d) - A(p)) psi, a problem of the same kind whose source lives in the
+perturbed cell only.  For a cross-section change the operator changes by dsigma_t psi - (dsigma_s / eps) psi_bar
+in that cell, i.e. the difference problem has the angle-dependent source
+    q_l = -(dsigma_t psi_l - (dsigma_s / eps) phi) / eps      (Q1 moments in cell K, zero elsewhere)
+with psi_l the forward solution's moments there (the standard scheme's four, or LMDG's cell average and the
+isotropic slopes).  dJ = sum g h^2 dphi_0 is then exact to the solver tolerance relative to dJ itself.  J is linear
+in q, so dJ/dq is checked by one difference solve with a unit source in the cell."""
+import copy
+
+import numpy as np
+import pytest
+
+from workloads.problems import config5
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve_phi(p, variant):
+    from paper_1907_01027_gb300 import Context
+    ctx = Context(p, variant, tol=1e-13, max_iters=20000)
+    _, phi, st, rc = ctx.solve()
+    ctx.close()
+    assert rc == 0, st
+    return phi
+
+
+@pytest.mark.parametrize("variant", ["std", "lm"])
+def test_adjoint_central_differences_256_s8(variant):
+    from paper_1907_01027_gb300 import Context
+    p = config5()
+    g = p.info["detector"]
+    cells = p.info["fd_cells"]
+    assert len(cells) == 32
+    ctx = Context(p, variant, tol=1e-13, max_iters=20000)
+    J, dss, dsa, dq, st = ctx.adjoint(g)
+    _, phi, _, rc = ctx.solve()
+    assert rc == 0
+    psi = ctx.get_psi()
+    ctx.close()
+    # the mixed-precision adjoint (FP32 sweeps, FP64 refinement) on the same cells
+    cm = Context(p, variant, tol=1e-12, precision=1)
+    Jm, dssm, dsam, dqm, _ = cm.adjoint(g)
+    cm.close()
+    h2, eps = p.h * p.h, p.eps
+    qd = np.zeros((p.nang, p.nx, 4))
+    for K in cells:
+        for field, ref, refm in (("sigma_s", dss, dssm), ("sigma_a", dsa, dsam)):
+            delta = 1e-3 * getattr(p, field)[K]
+            dJ = []
+            for d in (delta, -delta):
+                pp = copy.copy(p)
+                setattr(pp, field, getattr(p, field).copy())
+                getattr(pp, field)[K] += d
+                dsig_t = d / eps if field == "sigma_s" else eps * d
+                dsse = d / eps if field == "sigma_s" else 0.0
+                if variant == "std":
+                    qd[:, K, :] = -(dsig_t * psi[:, K, :] - dsse * phi[K][None, :]) / eps
+                else:
+                    qd[:, K, 0] = -(dsig_t * psi[:, K] - dsse * phi[K, 0]) / eps
+                    qd[:, K, 1:] = -((dsig_t - dsse) * phi[K, 1:])[None, :] / eps
+                pp.q = qd
+                pp.alpha = None
+                dJ.append(float(np.sum(g * h2 * _solve_phi(pp, variant)[:, 0])))
+                qd[:, K, :] = 0.0
+            fd = (dJ[0] - dJ[1]) / (2 * delta)
+            assert abs(fd - ref[K]) <= 1e-6 * abs(ref[K]) + 1e-12 * abs(J), (variant, field, K, fd, ref[K])
+            assert abs(fd - refm[K]) <= 1e-6 * abs(ref[K]) + 1e-12 * abs(J), (variant, "mixed", field, K, fd, refm[K])
+    for K in cells[:8]:
+        pq = copy.copy(p)
+        pq.q = np.zeros((p.nx, 4))
+        pq.q[K, 0] = 1.0
+        dJq = float(np.sum(g * h2 * _solve_phi(pq, variant)[:, 0]))
+        assert abs(dJq - dq[K]) <= 1e-9 * abs(dq[K]), (variant, K, dJq, dq[K])

@@ -76,3 +76,29 @@ def test_lowmem_dense_adjoint_finite_differences():
 def _Jlm(p, g):
     phi = dense.solve(p, "lm")["phi"]
     return float(np.sum(g * p.h * p.h * phi[:, 0]))
+
+
+def test_reversal_symmetry_holds_for_lm_but_not_rlm():
+    """Why the adjoint of RLMDG cannot be solved by the forward sweeps.  With Pi the direction reversal, the full
+    form satisfies B^T = Pi B Pi, and V_h^lm is closed under Pi, so the LMDG system A = E^T B E satisfies
+    A^T = Pi' A Pi': its adjoint is the forward scheme with the directions reversed (what lmdg_adjoint solves).
+    RLMDG is Petrov-Galerkin, A = E^T B Et with the upwind-reconstructed trial basis Et; reversing the directions
+    turns upwind into downwind reconstruction, so A^T is a different scheme (O(1) apart)."""
+    p = random_problem(3, 4, 0.7, 95, q_per_angle=False)
+    L, S, Q = dense.assemble(p)
+    B = L - S
+    na, nx = p.nang, p.nx
+    rev = [int(np.nonzero((np.abs(p.ox + p.ox[l]) < 1e-15) & (np.abs(p.oy + p.oy[l]) < 1e-15))[0][0])
+           for l in range(na)]
+    full = np.arange(na * nx * 4).reshape(na, nx, 4)
+    Pi = np.zeros((na * nx * 4,) * 2)
+    Pi[full.ravel(), full[rev].ravel()] = 1.0
+    assert np.abs(B.T - Pi @ B @ Pi).max() <= 1e-14 * np.abs(B).max()
+    red = np.arange(na * nx).reshape(na, nx)
+    perm = np.concatenate([red[rev].ravel(), na * nx + np.arange(3 * nx)])
+    E = dense.lm_basis(p)
+    A = E.T @ B @ E
+    assert np.abs(A.T - A[np.ix_(perm, perm)]).max() <= 1e-13 * np.abs(A).max()
+    Et = dense.rlm_trial_basis(p)
+    At = E.T @ B @ Et
+    assert np.abs(At.T - At[np.ix_(perm, perm)]).max() >= 1e-2 * np.abs(At).max()
