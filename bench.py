@@ -214,7 +214,7 @@ def run_reference(args, rank, ws):
 def run_gpu(args, rank, ws, dist):
     import numpy as np
     import torch
-    from paper_1907_01027_gb300 import Context, FP32, FP64, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
+    from paper_1907_01027_gb300 import Context, FP32, FP64, FP32_BF16STORE, SWEEP_FP32, SWEEP_STORE, SWEEP_SOURCE
     from paper_1907_01027_gb300 import RESID_F32X2, RESID_FP64
     from paper_1907_01027_gb300 import buildlib
     from workloads.problems import config4
@@ -335,36 +335,49 @@ def run_gpu(args, rank, ws, dist):
             ctx.close()
     out["gmres_time_to_1e-8"] = ttr
 
-    # storing sweep (recovery): HBM roofline of the FP32 Q1-DG sweep that writes psi (16 B per update)
+    # storing sweeps (recovery): HBM roofline of the FP32 sweeps that write the angular unknowns -- Q1-DG psi
+    # (16 B per update), LMDG psi0 in FP32 (4 B) and in bfloat16 (2 B)
+    hbm = peaks().get("hbm_gbs")
     x = torch.randn(p.nx, 4, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
-    c = ctxs["std"]
-    for _ in range(3):
-        c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
-    torch.cuda.synchronize()
-    reps = 5
-    e0.record()
-    for _ in range(reps):
-        flush.fill_(1.0)
-        c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
-    e1.record()
-    torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
-    e2.record()
-    for _ in range(reps):
-        flush.fill_(1.0)
-    e3.record()
-    torch.cuda.synchronize()
-    ms_store = (e0.elapsed_time(e1) - e2.elapsed_time(e3)) / reps
-    bytes_store = upd * 16 + p.nx * (32 + 4 * 3 + 16) + p.nx * 32
-    hbm = peaks().get("hbm_gbs")
-    ach = bytes_store / (ms_store / 1e3) / 1e9
-    out["roofline_storing_sweep"] = {"bound": "hbm", "kernel": "sweep_kernel<float, Q1-DG, store> + epilogue",
-                                     "achieved": ach, "peak": hbm, "unit": "GB/s",
-                                     "frac": ach / hbm if hbm else None, "ms": ms_store,
-                                     "algorithmic_bytes": bytes_store,
-                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    def storing(c, psi_bytes, kernel):
+        for _ in range(3):
+            c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+        torch.cuda.synchronize()
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            flush.fill_(1.0)
+            c.sweep(x, y, flags=SWEEP_FP32 | SWEEP_STORE | SWEEP_SOURCE)
+        e1.record()
+        torch.cuda.synchronize()
+        e2.record()
+        for _ in range(reps):
+            flush.fill_(1.0)
+        e3.record()
+        torch.cuda.synchronize()
+        ms = (e0.elapsed_time(e1) - e2.elapsed_time(e3)) / reps
+        nbytes = upd * psi_bytes + p.nx * (32 + 4 * 3 + 16) + p.nx * 32
+        ach = nbytes / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm if hbm else None, "ms": ms, "algorithmic_bytes": nbytes,
+                "psi_bytes_per_update": psi_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    bf = Context(p, "lm", precision=FP32_BF16STORE, device=local)
+    out["roofline_storing_sweep"] = storing(ctxs["std"], 16, "sweep_kernel<float, Q1-DG, store> + epilogue")
+    out["roofline_storing_sweeps"] = {
+        "std_fp32": out["roofline_storing_sweep"],
+        "lm_fp32": storing(ctxs["lm"], 4, "sweep_kernel<float, LMDG, store psi0 fp32> + epilogue"),
+        "lm_bf16": storing(bf, 2, "sweep_kernel<float, LMDG, store psi0 bf16> + epilogue")}
+    bf.close()
+
+    # diffusive regime: the same workload at eps = 1e-3, GMRES right-preconditioned by the vertex diffusion
+    # correction (precond = 2), time to 1e-8 with FP32 sweeps and FP64 residual sweeps against the FP64 solver
+    if not args.skip_diffusive:
+        out["gmres_time_to_1e-8_eps1e-3"] = diffusive_times(args, local)
 
     # end to end through the public API with host buffers: setup from host arrays, solve, phi back to host
     e2e_ms, e2e_upd = 0.0, 0
@@ -408,6 +421,44 @@ def run_gpu(args, rank, ws, dist):
     return 0
 
 
+# iteration caps of the eps = 1e-3 solves (GMRES iterations, all refinement steps)
+DIFFUSIVE_MAX_ITERS = {"std": 2000, "lm": 3000, "rlm": 1500}
+
+
+def diffusive_times(args, local):
+    """Time to 1e-8 at eps = 1e-3 on the 1024^2 S16 patch medium (sigma_t h from 0.1 to 10): per scheme the mixed
+    solver (FP32 sweeps, FP64 residual sweeps, FP64 refinement) and the FP64 solver, both with the vertex diffusion
+    correction, one timed solve each after the context's workspace is allocated."""
+    import numpy as np
+    import torch
+    from paper_1907_01027_gb300 import Context, FP32, FP64, RESID_FP64
+    from workloads.problems import config4
+    p = config4(eps=1e-3)
+    res = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for v in VARIANTS:
+        res[v] = {}
+        for mode, kw in (("mixed", dict(precision=FP32, resid=RESID_FP64)), ("fp64", dict(precision=FP64))):
+            if args.skip_fp64 and mode == "fp64":
+                continue
+            ctx = Context(p, v, precond=2, tol=1e-8, max_iters=DIFFUSIVE_MAX_ITERS[v], device=local, **kw)
+            ctx.precond_apply(np.zeros((p.nx, 4)))          # allocates the Krylov workspace outside the timing
+            torch.cuda.synchronize()
+            e0.record()
+            _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
+            e1.record()
+            torch.cuda.synchronize()
+            res[v][mode] = {"ms": e0.elapsed_time(e1), "status": rc, "iters": st["iters"],
+                            "refinements": st["refinements"], "resid": st["resid"] / st["resid0"],
+                            "sweeps_fp32": st["sweeps_fp32"], "sweeps_fp64": st["sweeps_fp64"],
+                            "sweep_ms_fp32": st["sweep_ms_fp32"], "sweep_ms_fp64": st["sweep_ms_fp64"]}
+            ctx.close()
+    res["note"] = ("status 0: converged to 1e-8; -5: iteration cap reached (resid is then the relative residual "
+                   "reached)")
+    return res
+
+
 def run_profile(args):
     """Small case for ncu: 512x512 cells, S16, the bench media; per pass the three FP32 non-storing sweeps (as
     inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2), the three
@@ -444,6 +495,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-diffusive", action="store_true", help="leave out the eps = 1e-3 solves")
     ap.add_argument("--profile", action="store_true", help="small fixed case for ncu captures")
     args = ap.parse_args()
     if args.profile:

@@ -5,14 +5,14 @@
  * and of the two low-memory schemes, the angular reduction fused into the sweep, GMRES on the
  * sweep-reduced systems, mixed-precision iterative refinement and the adjoint sweep.
  *
- * Problem (eq-main, Section 1): on a uniform n x n Cartesian mesh,
+ * Problem (eq-main, Section 1): on a uniform Cartesian mesh of nx x ny square cells (Section 2.1),
  *   Omega . grad Psi + (sigma_s/eps + eps sigma_a) Psi = (sigma_s/eps) Psi_bar + eps q,  Psi = alpha on inflow,
  * discretised by S_N collocation (eq:sn) and upwind DG with the Legendre Q1 basis (1, xi, eta, xi*eta) per
  * cell (eq-Ljk, eq-sndg-scheme).
  *
  * Conventions for every entry point:
- *   - Cell (i, j) (i along x, j along y) has index p = j*n + i.  Per-cell vectors are [n*n][4] doubles in the
- *     Legendre basis above ("moments"), cell-major.
+ *   - Cell (i, j) (i < nx along x, j < ny along y) has index p = j*nx + i.  Per-cell vectors are [nx*ny][4]
+ *     doubles in the Legendre basis above ("moments"), cell-major.  Below, N = nx*ny is the number of cells.
  *   - Return value: 0 on success, a negative LMDG_ERR_* code otherwise; lmdg_strerror() describes it.
  *   - Vectors passed to lmdg_sweep / lmdg_solve / lmdg_adjoint are DEVICE pointers (cudaMalloc'd memory of
  *     the context's device) unless LMDG_HOST_PTRS is set in flags, in which case they are host pointers and
@@ -34,7 +34,7 @@ typedef struct lmdg_ctx lmdg_ctx;
 /* Scheme: standard S_N-DG with the full Q1 space V_h (eq-sndg-scheme); low-memory LMDG with
  * V_h^lm = V_{h,0} + D_{h,1} (eq-gene-scheme, Section 3.2); reconstructed RLMDG (eq-rlmdg-vari,
  * Section 3.3); P0-DG, the S_N-DG scheme on the piecewise constants V_{h,0} (the comparison scheme of
- * Section 3.1: first order, without the diffusion limit).  For P0-DG the reduced vector keeps the [n*n][4]
+ * Section 3.1: first order, without the diffusion limit).  For P0-DG the reduced vector keeps the [N][4]
  * layout; its unknown is the cell average (entry 0) and entries 1..3 are carried by the identity. */
 enum { LMDG_STD = 0, LMDG_LM = 1, LMDG_RLM = 2, LMDG_P0 = 3 };
 
@@ -75,9 +75,9 @@ enum {
 };
 
 typedef struct {
-  int n;               /* cells per side (n >= 1) */
+  int nx, ny;          /* cells along x and along y (each >= 1, nx * ny <= 2^30) */
   double x0, y0;       /* lower-left corner */
-  double h;            /* cell side (> 0) */
+  double h;            /* cell side (> 0): the domain is [x0, x0 + nx h] x [y0, y0 + ny h] */
 } lmdg_mesh;
 
 typedef struct {
@@ -94,7 +94,9 @@ typedef struct {
   double tol;          /* relative residual target ||r_k|| <= tol ||r_0|| (default 1e-8) */
   double inner_tol;    /* FP32 modes: relative tolerance of each inner GMRES solve (default 1e-4) */
   int max_refine;      /* FP32 modes: cap on outer refinement steps (default 50) */
-  int precond;         /* 1 (default): right preconditioner diag(I, diag(B11))^-1 for LMDG/RLMDG; 0: none */
+  int precond;         /* right preconditioner of GMRES: 1 (default) diag(I, diag(B11))^-1 for LMDG/RLMDG (the
+                          identity for Q1-DG); 0 none; 2 the same followed by the vertex diffusion correction
+                          (lmdg_precond_apply) for the diffusive regime -- not for LMDG_P0 (LMDG_ERR_ARG) */
   long long spin_limit;/* polls of a readiness flag before a sweep reports LMDG_ERR_TIMEOUT (default 2^26) */
   int device;          /* CUDA device ordinal (default 0) */
   int suppress;        /* LMDG_RLM only, 1: no reconstruction across an interior face where sigma_s or sigma_a
@@ -130,24 +132,27 @@ typedef struct {
 int lmdg_default_options(lmdg_options *opt);
 
 /* Create a problem context (setup step: Section 2.1 data).  All inputs are host pointers and are copied.
- *   sigma_s, sigma_a : [n*n] per-cell cross sections, sigma_s >= 0, sigma_a >= 0, sigma_t > 0 everywhere.
- *   q                : source as Legendre moments; q_layout 0: [n*n] cell constants; 1: [n*n][4];
- *                      2: [n_Omega][n*n][4] angle dependent (Section 4.1 allows q to depend on angle).
- *   alpha            : inflow data, NULL for vacuum; otherwise [n_Omega][4][n][2]: per direction, side
- *                      (0 west x = x0, 1 east, 2 south y = y0, 3 north) and boundary face, the coefficients
+ *   sigma_s, sigma_a : [N] per-cell cross sections, sigma_s >= 0, sigma_a >= 0, sigma_t > 0 everywhere.
+ *   q                : source as Legendre moments; q_layout 0: [N] cell constants; 1: [N][4];
+ *                      2: [n_Omega][N][4] angle dependent (Section 4.1 allows q to depend on angle).
+ *   alpha            : inflow data (the boundary condition Psi = alpha on the inflow boundary, eq-main), NULL for
+ *                      vacuum.  alpha_layout 0: alpha points to one value, the same constant on every inflow face
+ *                      for every direction.  alpha_layout 1: [n_Omega][2 ny + 2 nx][2]: per direction the
+ *                      boundary faces of the west side (x = x0, ny faces by row j), the east side (ny), the south
+ *                      side (y = y0, nx faces by column i) and the north side (nx), each with the coefficients
  *                      (a0, a1) of alpha = a0 + a1 t along the face, t in [-1, 1] increasing with the global
  *                      coordinate.  Only inflow faces are read.  The reconstruction of RLMDG uses a0 as the
- *                      face-midpoint value of alpha (Section 3.3.1).
+ *                      face-midpoint value of alpha (Section 3.3.1).  Other layouts return LMDG_ERR_ARG.
  *   eps              : scaling parameter epsilon > 0 of eq-main.
  *   variant          : LMDG_STD, LMDG_LM, LMDG_RLM or LMDG_P0.
  *   opt              : NULL for defaults.
- * Device memory: O(n_Omega * n^2) for the angular-flux store, O(n^2) for the rest. */
+ * Device memory: O(n_Omega * N) for the angular-flux store, O(N) for the rest. */
 int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad,
                const double *sigma_s, const double *sigma_a, const double *q, int q_layout,
-               const double *alpha, double eps, int variant, const lmdg_options *opt);
+               const double *alpha, int alpha_layout, double eps, int variant, const lmdg_options *opt);
 
 /* One application of the sweep-reduced operator (one transport sweep over all directions with the angular
- * reduction fused into it), on vectors of [n*n][4] doubles:
+ * reduction fused into it), on vectors of [N][4] doubles:
  *   LMDG_STD : K x = x - P L^-1 M x  (eq-sndg-phi), x = Phi, the scalar-flux moments;
  *              b = P L^-1 Q.
  *   LMDG_LM  : K [X0; X1] of eq-lmdg-reducemat, evaluated as in eq-nonrec-block; x = (X0, X1) per cell;
@@ -158,8 +163,9 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
  *              b = its right-hand side minus K [0; z], z = B11^-1 Sigma Qtilde1.
  * With LMDG_SWEEP_SOURCE the call returns y = K x - b, so that the solution of lmdg_solve zeroes it (for the
  * low-memory variants this is the paper's system written for the shifted unknown X1 - z, i.e. GMRES started
- * from X1 = z).  LMDG_SWEEP_STORE keeps this sweep's angular unknowns: psi [n_Omega][n*n][4] for LMDG_STD,
- * psi0 [n_Omega][n*n] for the low-memory variants.  LMDG_SWEEP_FP32 / LMDG_SWEEP_F32X2 run the sweep in float /
+ * from X1 = z).  LMDG_SWEEP_STORE keeps this sweep's angular unknowns: psi [n_Omega][N][4] for LMDG_STD,
+ * psi0 [n_Omega][N] for the low-memory variants (bfloat16 for an FP32 sweep when the context's precision is
+ * LMDG_FP32_BF16STORE).  LMDG_SWEEP_FP32 / LMDG_SWEEP_F32X2 run the sweep in float /
  * float-float (x and y stay double); LMDG_SWEEP_F32X2 with LMDG_SWEEP_FP32 or LMDG_SWEEP_STORE returns
  * LMDG_ERR_ARG.  Asynchronous on stream for device pointers. */
 int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
@@ -169,38 +175,56 @@ int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *strea
  * FP32 modes: the first iterate comes from FP32 sweeps alone (an FP32 right-hand side and one FP32 GMRES
  * cycle); every later step computes the residual b - K x with an FP64 sweep, runs FP32-sweep GMRES on it and
  * updates x in FP64 (iterative refinement).  Convergence is ||b - K x|| <= tol ||b|| on FP64 residuals.
- *   x0  : initial guess [n*n][4] (NULL = zero), in the unknowns of lmdg_sweep with LMDG_SWEEP_SOURCE.
- *   x   : output [n*n][4], the converged unknowns (may be NULL).
- *   phi : output [n*n][4], the scalar-flux moments sum_l w_l psi_l of the discrete solution (may be NULL).
+ *   x0  : initial guess [N][4] (NULL = zero), in the unknowns of lmdg_sweep with LMDG_SWEEP_SOURCE.
+ *   x   : output [N][4], the converged unknowns (may be NULL).
+ *   phi : output [N][4], the scalar-flux moments sum_l w_l psi_l of the discrete solution (may be NULL).
  *   stats: may be NULL.
  * Returns LMDG_ERR_NOTCONV (with outputs written) if max_iters is reached. */
 int lmdg_solve(lmdg_ctx *ctx, const double *x0, double *x, double *phi, lmdg_stats *stats, int flags,
                void *stream);
 
 /* Copy the angular unknowns kept by the last storing sweep (lmdg_solve always stores) to psi:
- * LMDG_STD [n_Omega][n*n][4], low-memory variants [n_Omega][n*n] (cell averages psi0; the isotropic slopes
+ * LMDG_STD [n_Omega][N][4], low-memory variants [n_Omega][N] (cell averages psi0; the isotropic slopes
  * are the phi output of lmdg_solve).  Directions in the order given to lmdg_setup. */
 int lmdg_get_psi(lmdg_ctx *ctx, double *psi, int flags, void *stream);
 
-/* Adjoint sensitivities of the detector functional J = sum_K g_K int_K Psi_bar dx (g: [n*n] weights) with
+/* Adjoint sensitivities of the detector functional J = sum_K g_K int_K Psi_bar dx (g: [N] weights) with
  * respect to the per-cell sigma_s, sigma_a and the per-cell constant source q (no counterpart in the paper:
  * the discrete adjoint of its schemes), for LMDG_STD and LMDG_LM with q_layout 0 or 1.  Requires a centrally
  * symmetric quadrature (LMDG_ERR_QUAD otherwise): then the transpose of each direction's upwind block is the
  * block of the opposite direction, so the adjoint system is the forward reduced system with the detector
  * response as source; the forward angular flux is stored (FP64) and correlated cell by cell with the adjoint one
- * in a final sweep.  Outputs [n*n] each (any may be NULL) and J.  RLMDG (a Petrov-Galerkin scheme whose adjoint
+ * in a final sweep.  Outputs [N] each (any may be NULL) and J.  RLMDG (a Petrov-Galerkin scheme whose adjoint
  * has reconstructed test functions) returns LMDG_ERR_ARG. */
 int lmdg_adjoint(lmdg_ctx *ctx, const double *g, double *dJ_dsigma_s, double *dJ_dsigma_a,
                  double *dJ_dq, double *J, lmdg_stats *stats, int flags, void *stream);
 
-/* B11 = Sigma L11 Sigma^T - Sigma M1 of eq-lmdg-psi1 (the isotropic-slope block) applied to x [n*n][3]:
- * y [n*n][3].  Provided for the paper-literal reduced right-hand side and for checking. */
+/* B11 = Sigma L11 Sigma^T - Sigma M1 of eq-lmdg-psi1 (the isotropic-slope block) applied to x [N][3]:
+ * y [N][3].  Provided for the paper-literal reduced right-hand side and for checking. */
 int lmdg_b11_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
 
 /* Solve B11 z = r by conjugate gradients (B11 is SPD for centrally symmetric quadratures, Theorem
  * lem-B11) to relative residual tol; iters (may be NULL) receives the iteration count. */
 int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *iters, int flags,
                    void *stream);
+
+/* y = Minv x: the right preconditioner that lmdg_solve applies before every sweep, on [N][4] vectors (no
+ * counterpart in the paper, which leaves preconditioning to future work).  precond 1: the Jacobi scaling
+ * diag(I, diag(B11))^-1 of the low-memory schemes (identity for Q1-DG).  precond 2: that scaling, then the
+ * vertex diffusion correction u -> u + I_h D_a^-1 R_h (sigma_s/eps) u: K ~ D_t^-1 D_a on the slowly converging
+ * modes of the diffusive regime (D_t = -div D grad + sigma_t, D_a = -div D grad + eps sigma_a, D = 1/(3 sigma_t)),
+ * so K^-1 ~ I + D_a^-1 (sigma_s/eps).  D_a is each scheme's diffusion limit on the continuous Q1 functions of
+ * the (nx+1) x (ny+1) vertices (Section 3.1): int D grad d . grad v for Q1-DG (eq-lmdg-cg), int D Pi_0(grad d) .
+ * Pi_0(grad v) for LMDG and RLMDG (eq-difflimPF), plus int eps sigma_a d v and the vacuum boundary term
+ * sum over sides of A_n int d v (A_n = sum_{Omega.n > 0} w Omega.n); R_h tests the cell function against the
+ * vertex hat functions, I_h takes the bilinear interpolant's Legendre moments; for the low-memory schemes u
+ * holds (X0, X1) and the scalar-flux slopes are -X1.  D_a^-1 is one geometric multigrid V-cycle (bilinear
+ * prolongation, two components per coarse vertex below the finest level of the cell-average operator, Galerkin
+ * coarse operators, two damped block-Jacobi steps (omega = 0.7) before and after, dense coarsest solve up to
+ * 1156 unknowns, else 50 Jacobi steps; levels halve nx and ny while both are even and above 2), built by
+ * lmdg_setup.  x and y distinct; asynchronous on stream for
+ * device pointers. */
+int lmdg_precond_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
 
 /* Operator application that allocates nothing (no counterpart in the paper: it is a deployment variant of
  * lmdg_sweep's homogeneous mode, y = K x, for callers that cannot call cudaMalloc -- e.g. a host framework
@@ -225,8 +249,8 @@ int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, const double *
                        const double *w, const double *sigma_t, const double *sigma_s_over_eps,
                        const double *x, double *y, long long spin_limit, void *stream);
 
-/* Problem sizes of a context: n, n_Omega, variant. */
-int lmdg_info(const lmdg_ctx *ctx, int *n, int *n_omega, int *variant);
+/* Problem sizes of a context: cells along x and y, n_Omega, variant (any pointer may be NULL). */
+int lmdg_info(const lmdg_ctx *ctx, int *nx, int *ny, int *n_omega, int *variant);
 
 /* Free every device buffer of the context.  NULL is ignored. */
 void lmdg_destroy(lmdg_ctx *ctx);

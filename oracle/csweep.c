@@ -2,8 +2,9 @@
  *
  * TEST INFRASTRUCTURE ONLY: called from oracle/sweeps.py through ctypes; never linked into the product.
  *
- * Every routine handles ONE discrete ordinate Omega_l = (ox, oy) on a uniform n x n Cartesian mesh of cell
- * side h (cell (i, j) has index K = j*n + i) with the Legendre Q1 basis b = (1, xi, eta, xi*eta).  The
+ * Every routine handles ONE discrete ordinate Omega_l = (ox, oy) on a uniform ni x nj Cartesian mesh of square
+ * cells of side h (ni cells along x, nj along y; cell (i, j) has index K = j*ni + i) with the Legendre Q1 basis
+ * b = (1, xi, eta, xi*eta).  The
  * operator is the unweighted per-angle block of L in Appendix A (the factor w_l is applied by the caller):
  *
  *   L_{l,K}(u, b_r) = -int_K u Omega.grad b_r + int_{dK} u_hat Omega.nu_K b_r + int_K sigma_t u b_r   (eq-Ljk)
@@ -78,12 +79,12 @@ static void build_elem(double h, elem_t *e) {
 }
 
 /* neighbour index across face f of cell (i, j), or -1 on the boundary */
-static int nbr(int n, int i, int j, int f) {
+static int nbr(int ni, int nj, int i, int j, int f) {
   switch (f) {
-    case 0: return i > 0 ? j * n + i - 1 : -1;
-    case 1: return i < n - 1 ? j * n + i + 1 : -1;
-    case 2: return j > 0 ? (j - 1) * n + i : -1;
-    default: return j < n - 1 ? (j + 1) * n + i : -1;
+    case 0: return i > 0 ? j * ni + i - 1 : -1;
+    case 1: return i < ni - 1 ? j * ni + i + 1 : -1;
+    case 2: return j > 0 ? (j - 1) * ni + i : -1;
+    default: return j < nj - 1 ? (j + 1) * ni + i : -1;
   }
 }
 
@@ -102,28 +103,28 @@ static void diag_block(const elem_t *e, double ox, double oy, double sigt, doubl
 
 /* coupling of row block K to the upwind neighbours: out[r] = sum over inflow faces of
  * (Omega.nu) int_F u_{K'} b_r (K' interior neighbour) */
-static void inflow_terms(const elem_t *e, int n, int i, int j, double ox, double oy, const double *u,
+static void inflow_terms(const elem_t *e, int ni, int nj, int i, int j, double ox, double oy, const double *u,
                          double out[4]) {
   out[0] = out[1] = out[2] = out[3] = 0.0;
   for (int f = 0; f < 4; ++f) {
     double on = ox * e->nrm[f][0] + oy * e->nrm[f][1];
-    int k = nbr(n, i, j, f);
+    int k = nbr(ni, nj, i, j, f);
     if (on < 0 && k >= 0)
       for (int r = 0; r < 4; ++r)
         for (int s = 0; s < 4; ++s) out[r] += on * e->nbrf[f][r][s] * u[4 * k + s];
   }
 }
 
-/* out = L_l u for one angle (unweighted); u, out: [n*n][4] */
-void osw_apply_L(int n, double h, double ox, double oy, const double *sigt, const double *u, double *out) {
+/* out = L_l u for one angle (unweighted); u, out: [ni*nj][4] */
+void osw_apply_L(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *u, double *out) {
   elem_t e;
   build_elem(h, &e);
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      int K = j * n + i;
+  for (int j = 0; j < nj; ++j)
+    for (int i = 0; i < ni; ++i) {
+      int K = j * ni + i;
       double A[4][4], c[4];
       diag_block(&e, ox, oy, sigt[K], A);
-      inflow_terms(&e, n, i, j, ox, oy, u, c);
+      inflow_terms(&e, ni, nj, i, j, ox, oy, u, c);
       for (int r = 0; r < 4; ++r) {
         double s = c[r];
         for (int q = 0; q < 4; ++q) s += A[r][q] * u[4 * K + q];
@@ -153,19 +154,19 @@ static void solve4(double A[4][4], double b[4], double x[4]) {
   }
 }
 
-/* Solve L_l u = b (unweighted block) by an upwind sweep.  b, u: [n*n][4]. */
-void osw_sweep_L(int n, double h, double ox, double oy, const double *sigt, const double *b, double *u) {
+/* Solve L_l u = b (unweighted block) by an upwind sweep.  b, u: [ni*nj][4]. */
+void osw_sweep_L(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *b, double *u) {
   elem_t e;
   build_elem(h, &e);
-  memset(u, 0, sizeof(double) * 4 * (size_t)n * n);
-  for (int jj = 0; jj < n; ++jj) {
-    int j = oy > 0 ? jj : n - 1 - jj;
-    for (int ii = 0; ii < n; ++ii) {
-      int i = ox > 0 ? ii : n - 1 - ii;
-      int K = j * n + i;
+  memset(u, 0, sizeof(double) * 4 * (size_t)ni * nj);
+  for (int jj = 0; jj < nj; ++jj) {
+    int j = oy > 0 ? jj : nj - 1 - jj;
+    for (int ii = 0; ii < ni; ++ii) {
+      int i = ox > 0 ? ii : ni - 1 - ii;
+      int K = j * ni + i;
       double A[4][4], c[4], rhs[4];
       diag_block(&e, ox, oy, sigt[K], A);
-      inflow_terms(&e, n, i, j, ox, oy, u, c);
+      inflow_terms(&e, ni, nj, i, j, ox, oy, u, c);
       for (int r = 0; r < 4; ++r) rhs[r] = b[4 * K + r] - c[r];
       solve4(A, rhs, &u[4 * K]);
     }
@@ -173,22 +174,23 @@ void osw_sweep_L(int n, double h, double ox, double oy, const double *sigt, cons
 }
 
 /* Solve L00 u0 = b0 for one angle: the rows and columns of L restricted to the piecewise constants
- * (V_{h,0}, Section 3.2).  b0, u0: [n*n]. */
-void osw_sweep_L00(int n, double h, double ox, double oy, const double *sigt, const double *b0, double *u0) {
+ * (V_{h,0}, Section 3.2).  b0, u0: [ni*nj]. */
+void osw_sweep_L00(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *b0,
+                   double *u0) {
   elem_t e;
   build_elem(h, &e);
-  memset(u0, 0, sizeof(double) * (size_t)n * n);
-  for (int jj = 0; jj < n; ++jj) {
-    int j = oy > 0 ? jj : n - 1 - jj;
-    for (int ii = 0; ii < n; ++ii) {
-      int i = ox > 0 ? ii : n - 1 - ii;
-      int K = j * n + i;
+  memset(u0, 0, sizeof(double) * (size_t)ni * nj);
+  for (int jj = 0; jj < nj; ++jj) {
+    int j = oy > 0 ? jj : nj - 1 - jj;
+    for (int ii = 0; ii < ni; ++ii) {
+      int i = ox > 0 ? ii : ni - 1 - ii;
+      int K = j * ni + i;
       double A[4][4];
       diag_block(&e, ox, oy, sigt[K], A);
       double c = 0.0;
       for (int f = 0; f < 4; ++f) {
         double on = ox * e.nrm[f][0] + oy * e.nrm[f][1];
-        int k = nbr(n, i, j, f);
+        int k = nbr(ni, nj, i, j, f);
         if (on < 0 && k >= 0) c += on * e.nbrf[f][0][0] * u0[k];
       }
       u0[K] = (b0[K] - c) / A[0][0];
@@ -204,9 +206,9 @@ void osw_sweep_L00(int n, double h, double ox, double oy, const double *sigt, co
  * across such a face is taken as zero.  star (RLMDG*, Section 4.1): from the third cell on the difference is
  * the centre slope of the quadratic through the cell and its two upwind neighbours, (3u_i - 4u_{i-1} +
  * u_{i-2}) / (2h); the second cell keeps the two-cell difference. */
-static void recon0(int n, double h, double ox, double oy, const double *u0, const unsigned char *supp, int star,
-                   int i, int j, double sl[2]) {
-  int K = j * n + i;
+static void recon0(int ni, int nj, double h, double ox, double oy, const double *u0, const unsigned char *supp,
+                   int star, int i, int j, double sl[2]) {
+  int K = j * ni + i;
   unsigned m = supp ? supp[K] : 0u;
   double dx, dy;
   if (ox > 0) {
@@ -215,43 +217,43 @@ static void recon0(int n, double h, double ox, double oy, const double *u0, cons
     else if (star && i >= 2) dx = (3 * u0[K] - 4 * u0[K - 1] + u0[K - 2]) / (2 * h);
     else dx = (u0[K] - u0[K - 1]) / h;
   } else {
-    if (i == n - 1) dx = (0.0 - u0[K]) / (h / 2);
+    if (i == ni - 1) dx = (0.0 - u0[K]) / (h / 2);
     else if (m & 2u) dx = 0.0;
-    else if (star && i <= n - 3) dx = -(3 * u0[K] - 4 * u0[K + 1] + u0[K + 2]) / (2 * h);
+    else if (star && i <= ni - 3) dx = -(3 * u0[K] - 4 * u0[K + 1] + u0[K + 2]) / (2 * h);
     else dx = (u0[K + 1] - u0[K]) / h;
   }
   if (oy > 0) {
     if (j == 0) dy = (u0[K] - 0.0) / (h / 2);
     else if (m & 4u) dy = 0.0;
-    else if (star && j >= 2) dy = (3 * u0[K] - 4 * u0[K - n] + u0[K - 2 * n]) / (2 * h);
-    else dy = (u0[K] - u0[K - n]) / h;
+    else if (star && j >= 2) dy = (3 * u0[K] - 4 * u0[K - ni] + u0[K - 2 * ni]) / (2 * h);
+    else dy = (u0[K] - u0[K - ni]) / h;
   } else {
-    if (j == n - 1) dy = (0.0 - u0[K]) / (h / 2);
+    if (j == nj - 1) dy = (0.0 - u0[K]) / (h / 2);
     else if (m & 8u) dy = 0.0;
-    else if (star && j <= n - 3) dy = -(3 * u0[K] - 4 * u0[K + n] + u0[K + 2 * n]) / (2 * h);
-    else dy = (u0[K + n] - u0[K]) / h;
+    else if (star && j <= nj - 3) dy = -(3 * u0[K] - 4 * u0[K + ni] + u0[K + 2 * ni]) / (2 * h);
+    else dy = (u0[K + ni] - u0[K]) / h;
   }
   sl[0] = 0.5 * h * dx;
   sl[1] = 0.5 * h * dy;
 }
 
 /* row 0 of L_l applied to the trial function u0 b0 + R u0 at cell (i, j), given u0 on K and upwind cells */
-static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, double sigt, const double *u0,
-                       const unsigned char *supp, int star, int i, int j) {
-  int K = j * n + i;
+static double row0_rec(const elem_t *e, int ni, int nj, double h, double ox, double oy, double sigt,
+                       const double *u0, const unsigned char *supp, int star, int i, int j) {
+  int K = j * ni + i;
   double A[4][4], uK[4], sl[2];
   diag_block(e, ox, oy, sigt, A);
-  recon0(n, h, ox, oy, u0, supp, star, i, j, sl);
+  recon0(ni, nj, h, ox, oy, u0, supp, star, i, j, sl);
   uK[0] = u0[K]; uK[1] = sl[0]; uK[2] = sl[1]; uK[3] = 0.0;
   double s = 0.0;
   for (int q = 0; q < 4; ++q) s += A[0][q] * uK[q];
   for (int f = 0; f < 4; ++f) {
     double on = ox * e->nrm[f][0] + oy * e->nrm[f][1];
-    int k = nbr(n, i, j, f);
+    int k = nbr(ni, nj, i, j, f);
     if (on < 0 && k >= 0) {
-      int ki = k % n, kj = k / n;
+      int ki = k % ni, kj = k / ni;
       double uk[4], sk[2];
-      recon0(n, h, ox, oy, u0, supp, star, ki, kj, sk);
+      recon0(ni, nj, h, ox, oy, u0, supp, star, ki, kj, sk);
       uk[0] = u0[k]; uk[1] = sk[0]; uk[2] = sk[1]; uk[3] = 0.0;
       for (int q = 0; q < 4; ++q) s += on * e->nbrf[f][0][q] * uk[q];
     }
@@ -262,22 +264,22 @@ static double row0_rec(const elem_t *e, int n, double h, double ox, double oy, d
 /* Solve Ltilde00 u0 = b0 for one angle, Ltilde00 = L00 + L01 R (Section 3.3.2): row 0 of L applied to the
  * reconstructed trial function.  The reconstruction at K uses only K and its upwind neighbours, so the
  * system is lower triangular in sweep order; each cell's equation is affine in u0[K] and is solved from two
- * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [n*n]; supp: suppression bits as in recon0, or NULL; star:
- * the three-cell reconstruction. */
-void osw_sweep_Lt00(int n, double h, double ox, double oy, const double *sigt, const double *b0, double *u0,
-                    const unsigned char *supp, int star) {
+ * evaluations (u0[K] = 0 and u0[K] = 1).  b0, u0: [ni*nj]; supp: suppression bits as in recon0, or NULL;
+ * star: the three-cell reconstruction. */
+void osw_sweep_Lt00(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *b0,
+                    double *u0, const unsigned char *supp, int star) {
   elem_t e;
   build_elem(h, &e);
-  memset(u0, 0, sizeof(double) * (size_t)n * n);
-  for (int jj = 0; jj < n; ++jj) {
-    int j = oy > 0 ? jj : n - 1 - jj;
-    for (int ii = 0; ii < n; ++ii) {
-      int i = ox > 0 ? ii : n - 1 - ii;
-      int K = j * n + i;
+  memset(u0, 0, sizeof(double) * (size_t)ni * nj);
+  for (int jj = 0; jj < nj; ++jj) {
+    int j = oy > 0 ? jj : nj - 1 - jj;
+    for (int ii = 0; ii < ni; ++ii) {
+      int i = ox > 0 ? ii : ni - 1 - ii;
+      int K = j * ni + i;
       u0[K] = 0.0;
-      double r0 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, star, i, j);
+      double r0 = row0_rec(&e, ni, nj, h, ox, oy, sigt[K], u0, supp, star, i, j);
       u0[K] = 1.0;
-      double r1 = row0_rec(&e, n, h, ox, oy, sigt[K], u0, supp, star, i, j);
+      double r1 = row0_rec(&e, ni, nj, h, ox, oy, sigt[K], u0, supp, star, i, j);
       u0[K] = (b0[K] - r0) / (r1 - r0);
     }
   }
@@ -297,12 +299,13 @@ void osw_elem_tables(double h, double *out) {
 /* out = L_l^T u for one angle (transpose of the unweighted block of Appendix A).  Row block K of L^T collects
  * the transposed diagonal block of K and the transposed coupling blocks L[K', K] of every cell K' that takes
  * its inflow from K (the downwind neighbours of K). */
-void osw_apply_LT(int n, double h, double ox, double oy, const double *sigt, const double *u, double *out) {
+void osw_apply_LT(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *u,
+                  double *out) {
   elem_t e;
   build_elem(h, &e);
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      int K = j * n + i;
+  for (int j = 0; j < nj; ++j)
+    for (int i = 0; i < ni; ++i) {
+      int K = j * ni + i;
       double A[4][4];
       diag_block(&e, ox, oy, sigt[K], A);
       double s[4] = {0, 0, 0, 0};
@@ -310,7 +313,7 @@ void osw_apply_LT(int n, double h, double ox, double oy, const double *sigt, con
         for (int q = 0; q < 4; ++q) s[r] += A[q][r] * u[4 * K + q];
       /* K' = neighbour across face f of K; K is K''s inflow neighbour across the opposite face g of K' */
       for (int f = 0; f < 4; ++f) {
-        int k2 = nbr(n, i, j, f);
+        int k2 = nbr(ni, nj, i, j, f);
         if (k2 < 0) continue;
         int g = f ^ 1;                       /* W<->E, S<->N */
         double on = ox * e.nrm[g][0] + oy * e.nrm[g][1];
@@ -325,22 +328,22 @@ void osw_apply_LT(int n, double h, double ox, double oy, const double *sigt, con
 /* Solve L_l^T u = b (unweighted block) by back substitution: L_l is block lower triangular in upwind order, so
  * its transpose is solved in the reverse order, each cell's transposed diagonal block against b minus the
  * transposed couplings to its (already solved) downwind neighbours. */
-void osw_sweep_LT(int n, double h, double ox, double oy, const double *sigt, const double *b, double *u) {
+void osw_sweep_LT(int ni, int nj, double h, double ox, double oy, const double *sigt, const double *b, double *u) {
   elem_t e;
   build_elem(h, &e);
-  memset(u, 0, sizeof(double) * 4 * (size_t)n * n);
-  for (int jj = n - 1; jj >= 0; --jj) {
-    int j = oy > 0 ? jj : n - 1 - jj;
-    for (int ii = n - 1; ii >= 0; --ii) {
-      int i = ox > 0 ? ii : n - 1 - ii;
-      int K = j * n + i;
+  memset(u, 0, sizeof(double) * 4 * (size_t)ni * nj);
+  for (int jj = nj - 1; jj >= 0; --jj) {
+    int j = oy > 0 ? jj : nj - 1 - jj;
+    for (int ii = ni - 1; ii >= 0; --ii) {
+      int i = ox > 0 ? ii : ni - 1 - ii;
+      int K = j * ni + i;
       double A[4][4], At[4][4], rhs[4];
       diag_block(&e, ox, oy, sigt[K], A);
       for (int r = 0; r < 4; ++r)
         for (int q = 0; q < 4; ++q) At[r][q] = A[q][r];
       for (int r = 0; r < 4; ++r) rhs[r] = b[4 * K + r];
       for (int f = 0; f < 4; ++f) {
-        int k2 = nbr(n, i, j, f);
+        int k2 = nbr(ni, nj, i, j, f);
         if (k2 < 0) continue;
         int g = f ^ 1;
         double on = ox * e.nrm[g][0] + oy * e.nrm[g][1];

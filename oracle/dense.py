@@ -71,14 +71,15 @@ def _ref_integrals(h):
     return mass, vol, selfF, nbrF, normals
 
 
-def _neighbour(n, i, j, f):
+def _neighbour(n, m, i, j, f):
+    """Neighbour (i', j') across face f of cell (i, j) on n x m cells, or None on the boundary."""
     if f == 0:
         return (i - 1, j) if i > 0 else None
     if f == 1:
         return (i + 1, j) if i < n - 1 else None
     if f == 2:
         return (i, j - 1) if j > 0 else None
-    return (i, j + 1) if j < n - 1 else None
+    return (i, j + 1) if j < m - 1 else None
 
 
 def _face_alpha_integrals(alpha_l, n, i, j, f, h):
@@ -99,9 +100,9 @@ def _face_alpha_integrals(alpha_l, n, i, j, f, h):
 def assemble(p):
     """Global matrices of Appendix A on the full space V_h: returns (Lmat, Smat, Qvec) with B = L - S.
 
-    Index of the basis function xi^{l,p,r}: (l * n_x + p) * 4 + r, cell p = j * n + i.
+    Index of the basis function xi^{l,p,r}: (l * n_x + p) * 4 + r, cell p = j * n + i (n cells along x, m along y).
     """
-    n, h, nx, na = p.n, p.h, p.nx, p.nang
+    n, m, h, nx, na = p.n, p.rows, p.h, p.nx, p.nang
     mass, vol, selfF, nbrF, normals = _ref_integrals(h)
     sig_t = p.sigma_s / p.eps + p.eps * p.sigma_a
     dim = na * nx * 4
@@ -111,7 +112,7 @@ def assemble(p):
     for l in range(na):
         om = np.array([p.ox[l], p.oy[l]])
         wl = p.w[l]
-        for j in range(n):
+        for j in range(m):
             for i in range(n):
                 K = j * n + i
                 rows = slice((l * nx + K) * 4, (l * nx + K) * 4 + 4)
@@ -119,7 +120,7 @@ def assemble(p):
                 L[rows, rows] += wl * (-(om[0] * vol[0] + om[1] * vol[1]) + sig_t[K] * mass)
                 for f in range(4):
                     on = om @ normals[f]
-                    nb = _neighbour(n, i, j, f)
+                    nb = _neighbour(n, m, i, j, f)
                     if on > 0:                             # outflow: upwind trace is the interior one
                         L[rows, rows] += wl * on * selfF[f]
                     elif nb is not None:                   # inflow from the neighbour
@@ -144,8 +145,8 @@ def assemble(p):
 def _same_material(p):
     """(sx, sy): sx[j, f] is True when cells (f, j) and (f + 1, j) have equal (sigma_s, sigma_a), sy[f, i]
     likewise for cells (i, f) and (i, f + 1)."""
-    n = p.n
-    ss, sa = p.sigma_s.reshape(n, n), p.sigma_a.reshape(n, n)
+    n, m = p.n, p.rows
+    ss, sa = p.sigma_s.reshape(m, n), p.sigma_a.reshape(m, n)
     sx = (ss[:, 1:] == ss[:, :-1]) & (sa[:, 1:] == sa[:, :-1])
     sy = (ss[1:, :] == ss[:-1, :]) & (sa[1:, :] == sa[:-1, :])
     return sx, sy
@@ -165,36 +166,36 @@ def reconstruct(p, u0, alpha, suppress=False, three_cell=False):
     neighbours, (3 u_i - 4 u_{i-1} + u_{i-2}) / (2h); the second cell keeps the two-cell difference and the
     inflow cell the boundary difference.
     """
-    n, h, na = p.n, p.h, p.nang
-    out = np.zeros((na, n * n, 4))
+    n, m, h, na = p.n, p.rows, p.h, p.nang
+    out = np.zeros((na, n * m, 4))
     same_x, same_y = _same_material(p) if suppress else (None, None)
     for l in range(na):
-        U = u0[l].reshape(n, n)              # [j][i]
-        dx = np.zeros((n, n))
-        dy = np.zeros((n, n))
+        U = u0[l].reshape(m, n)              # [j][i]
+        dx = np.zeros((m, n))
+        dy = np.zeros((m, n))
         if p.ox[l] > 0:                      # delta^-_x
             dx[:, 1:] = (U[:, 1:] - U[:, :-1]) / h
             if three_cell:
                 dx[:, 2:] = (3 * U[:, 2:] - 4 * U[:, 1:-1] + U[:, :-2]) / (2 * h)
-            aW = alpha[l, 0, :, 0] if alpha is not None else np.zeros(n)
+            aW = alpha[l, 0, :m, 0] if alpha is not None else np.zeros(m)
             dx[:, 0] = (U[:, 0] - aW) / (h / 2)
         else:                                # delta^+_x
             dx[:, :-1] = (U[:, 1:] - U[:, :-1]) / h
             if three_cell:
                 dx[:, :-2] = -(3 * U[:, :-2] - 4 * U[:, 1:-1] + U[:, 2:]) / (2 * h)
-            aE = alpha[l, 1, :, 0] if alpha is not None else np.zeros(n)
+            aE = alpha[l, 1, :m, 0] if alpha is not None else np.zeros(m)
             dx[:, -1] = (aE - U[:, -1]) / (h / 2)
         if p.oy[l] > 0:
             dy[1:, :] = (U[1:, :] - U[:-1, :]) / h
             if three_cell:
                 dy[2:, :] = (3 * U[2:, :] - 4 * U[1:-1, :] + U[:-2, :]) / (2 * h)
-            aS = alpha[l, 2, :, 0] if alpha is not None else np.zeros(n)
+            aS = alpha[l, 2, :n, 0] if alpha is not None else np.zeros(n)
             dy[0, :] = (U[0, :] - aS) / (h / 2)
         else:
             dy[:-1, :] = (U[1:, :] - U[:-1, :]) / h
             if three_cell:
                 dy[:-2, :] = -(3 * U[:-2, :] - 4 * U[1:-1, :] + U[2:, :]) / (2 * h)
-            aN = alpha[l, 3, :, 0] if alpha is not None else np.zeros(n)
+            aN = alpha[l, 3, :n, 0] if alpha is not None else np.zeros(n)
             dy[-1, :] = (aN - U[-1, :]) / (h / 2)
         if suppress:
             if p.ox[l] > 0:

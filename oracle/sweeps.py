@@ -41,10 +41,10 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         for name in ("osw_apply_L", "osw_sweep_L", "osw_sweep_L00", "osw_apply_LT", "osw_sweep_LT"):
             f = getattr(lib, name)
-            f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
             f.restype = None
-        lib.osw_sweep_Lt00.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
-                                       ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int]
+        lib.osw_sweep_Lt00.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       dp, dp, dp, ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int]
         lib.osw_sweep_Lt00.restype = None
         lib.osw_elem_tables.argtypes = [ctypes.c_double, dp]
         lib.osw_elem_tables.restype = None
@@ -73,7 +73,7 @@ class SweepOracle:
         self.p = p
         self.literal_b11 = literal_b11
         self.three_cell = three_cell
-        self.n, self.h, self.nx, self.na = p.n, p.h, p.nx, p.nang
+        self.n, self.m, self.h, self.nx, self.na = p.n, p.rows, p.h, p.nx, p.nang
         self.suppress = suppress
         self.supp = self._suppression_bits() if suppress else None
         self.sigt = np.ascontiguousarray(p.sigma_s / p.eps + p.eps * p.sigma_a, dtype=np.float64)
@@ -87,13 +87,13 @@ class SweepOracle:
         """Interior faces where (sigma_s, sigma_a) jumps: per cell, bit 1 west, 2 east, 4 south, 8 north.  With
         ``suppress`` the RLMDG reconstruction takes no difference across these faces (the remedy for the kinks
         at cross-section discontinuities, Section 4)."""
-        n, p = self.n, self.p
-        ss, sa = p.sigma_s.reshape(n, n), p.sigma_a.reshape(n, n)
-        bits = np.zeros((n, n), dtype=np.uint8)
-        for j in range(n):
+        n, m, p = self.n, self.m, self.p
+        ss, sa = p.sigma_s.reshape(m, n), p.sigma_a.reshape(m, n)
+        bits = np.zeros((m, n), dtype=np.uint8)
+        for j in range(m):
             for i in range(n):
                 for bit, (jj, ii) in ((1, (j, i - 1)), (2, (j, i + 1)), (4, (j - 1, i)), (8, (j + 1, i))):
-                    if 0 <= ii < n and 0 <= jj < n and (ss[j, i] != ss[jj, ii] or sa[j, i] != sa[jj, ii]):
+                    if 0 <= ii < n and 0 <= jj < m and (ss[j, i] != ss[jj, ii] or sa[j, i] != sa[jj, ii]):
                         bits[j, i] |= bit
         return bits.ravel()
 
@@ -101,7 +101,8 @@ class SweepOracle:
     def _call(self, name, l, a, size):
         out = np.zeros(size)
         a = np.ascontiguousarray(a, dtype=np.float64)
-        args = [self.n, self.h, float(self.p.ox[l]), float(self.p.oy[l]), _ptr(self.sigt), _ptr(a), _ptr(out)]
+        args = [self.n, self.m, self.h, float(self.p.ox[l]), float(self.p.oy[l]), _ptr(self.sigt), _ptr(a),
+                _ptr(out)]
         if name == "osw_sweep_Lt00":
             args.append(None if self.supp is None else self.supp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
             args.append(1 if self.three_cell else 0)
@@ -144,18 +145,18 @@ class SweepOracle:
         return p.w[l] * out
 
     def _boundary(self, l):
-        p, n, h = self.p, self.n, self.h
+        p, n, m, h = self.p, self.n, self.m, self.h
         g, gw = np.polynomial.legendre.leggauss(3)
-        out = np.zeros((n, n, 4))                    # [j][i][r]
+        out = np.zeros((m, n, 4))                    # [j][i][r]
         ox, oy = p.ox[l], p.oy[l]
-        # (side, Omega.nu, cell slice, own reference coordinates of the face points)
-        sides = [(0, -ox, (slice(None), 0), (-np.ones(3), g)), (1, ox, (slice(None), n - 1), (np.ones(3), g)),
-                 (2, -oy, (0, slice(None)), (g, -np.ones(3))), (3, oy, (n - 1, slice(None)), (g, np.ones(3)))]
-        for side, on, sl, (xi, eta) in sides:
+        # (side, Omega.nu, cell slice, own reference coordinates of the face points, faces of the side)
+        sides = [(0, -ox, (slice(None), 0), (-np.ones(3), g), m), (1, ox, (slice(None), n - 1), (np.ones(3), g), m),
+                 (2, -oy, (0, slice(None)), (g, -np.ones(3)), n), (3, oy, (m - 1, slice(None)), (g, np.ones(3)), n)]
+        for side, on, sl, (xi, eta), nf in sides:
             if on >= 0:
                 continue
             B = np.stack([np.ones(3), xi, eta, xi * eta])           # [r][pt]
-            a = p.alpha[l, side]                                    # [n][2]
+            a = p.alpha[l, side, :nf]                               # [faces][2]
             vals = a[:, 0:1] + a[:, 1:2] * g[None, :]               # [face][pt]
             integ = (vals * gw[None, :]) @ B.T * (h / 2.0)          # [face][r]
             out[sl] += -on * integ
@@ -286,40 +287,40 @@ class SweepOracle:
     def R(self, l, u0, alpha=None):
         """R_alpha Pi_0 for angle l: Legendre slope coefficients [n_x][2] ((h/2) delta_x, (h/2) delta_y);
         with alpha None this is the linear part R, otherwise R u0 + r_alpha."""
-        n, h, p = self.n, self.h, self.p
-        U = u0.reshape(n, n)
-        bw = np.zeros(n) if alpha is None else alpha[l, 0, :, 0]
-        be = np.zeros(n) if alpha is None else alpha[l, 1, :, 0]
-        bs = np.zeros(n) if alpha is None else alpha[l, 2, :, 0]
-        bn = np.zeros(n) if alpha is None else alpha[l, 3, :, 0]
+        n, m, h, p = self.n, self.m, self.h, self.p
+        U = u0.reshape(m, n)
+        bw = np.zeros(m) if alpha is None else alpha[l, 0, :m, 0]
+        be = np.zeros(m) if alpha is None else alpha[l, 1, :m, 0]
+        bs = np.zeros(n) if alpha is None else alpha[l, 2, :n, 0]
+        bn = np.zeros(n) if alpha is None else alpha[l, 3, :n, 0]
         if p.ox[l] > 0:
             left = np.concatenate([bw[:, None], U[:, :-1]], axis=1)
-            sp = np.concatenate([np.full((n, 1), h / 2), np.full((n, n - 1), h)], axis=1)
+            sp = np.concatenate([np.full((m, 1), h / 2), np.full((m, n - 1), h)], axis=1)
             dx = (U - left) / sp
             if self.three_cell and n > 2:      # RLMDG*: quadratic through three upwind cell averages
                 dx[:, 2:] = (3 * U[:, 2:] - 4 * U[:, 1:-1] + U[:, :-2]) / (2 * h)
         else:
             right = np.concatenate([U[:, 1:], be[:, None]], axis=1)
-            sp = np.concatenate([np.full((n, n - 1), h), np.full((n, 1), h / 2)], axis=1)
+            sp = np.concatenate([np.full((m, n - 1), h), np.full((m, 1), h / 2)], axis=1)
             dx = (right - U) / sp
             if self.three_cell and n > 2:
                 dx[:, :-2] = (-3 * U[:, :-2] + 4 * U[:, 1:-1] - U[:, 2:]) / (2 * h)
         if p.oy[l] > 0:
             down = np.concatenate([bs[None, :], U[:-1, :]], axis=0)
-            sp = np.concatenate([np.full((1, n), h / 2), np.full((n - 1, n), h)], axis=0)
+            sp = np.concatenate([np.full((1, n), h / 2), np.full((m - 1, n), h)], axis=0)
             dy = (U - down) / sp
-            if self.three_cell and n > 2:
+            if self.three_cell and m > 2:
                 dy[2:, :] = (3 * U[2:, :] - 4 * U[1:-1, :] + U[:-2, :]) / (2 * h)
         else:
             up = np.concatenate([U[1:, :], bn[None, :]], axis=0)
-            sp = np.concatenate([np.full((n - 1, n), h), np.full((1, n), h / 2)], axis=0)
+            sp = np.concatenate([np.full((m - 1, n), h), np.full((1, n), h / 2)], axis=0)
             dy = (up - U) / sp
-            if self.three_cell and n > 2:
+            if self.three_cell and m > 2:
                 dy[:-2, :] = (-3 * U[:-2, :] + 4 * U[1:-1, :] - U[2:, :]) / (2 * h)
         if self.supp is not None:
-            m = self.supp.reshape(n, n)
-            dx = np.where(m & (1 if p.ox[l] > 0 else 2), 0.0, dx)
-            dy = np.where(m & (4 if p.oy[l] > 0 else 8), 0.0, dy)
+            bits = self.supp.reshape(m, n)
+            dx = np.where(bits & (1 if p.ox[l] > 0 else 2), 0.0, dx)
+            dy = np.where(bits & (4 if p.oy[l] > 0 else 8), 0.0, dy)
         return np.stack([0.5 * h * dx.ravel(), 0.5 * h * dy.ravel()], axis=1)
 
     def r_alpha(self, l):
@@ -444,14 +445,16 @@ class SweepOracle:
         return np.array(cols).T
 
     def solve(self, variant, tol=1e-12, restart=30, maxiter=20000, direct=None, x0=None, precond=None,
-              dsa_cycles=None):
+              dsa_cycles=None, mg=None):
         """Solve the reduced system and recover the solution.  Returns a dict like ``dense.solve`` plus
         ``X`` (reduced unknowns [n_x][4]) and ``iters``.
 
         ``precond='jacobi'`` (default for the low-memory variants) right-preconditions GMRES by
         diag(I, diag(B11))^-1, which leaves the residual of the original system unchanged; ``precond='dsa'``
         adds the diffusion correction of the cell averages (:mod:`oracle.dsa`) to it (to the identity for the
-        standard scheme and P0-DG), solved exactly or (``dsa_cycles``) by that many multigrid V-cycles."""
+        standard scheme and P0-DG), solved exactly or (``dsa_cycles``) by that many multigrid V-cycles;
+        ``precond='vdsa'`` is the vertex diffusion correction of :mod:`oracle.vdsa` (each scheme's own diffusion
+        limit) after the Jacobi scaling, its solve exact or ``dsa_cycles`` V-cycles (``mg``: multigrid options)."""
         if precond is None:
             precond = "none" if variant in ("std", "p0") else "jacobi"
         b = self.rhs(variant).ravel()
@@ -463,9 +466,13 @@ class SweepOracle:
             X = np.linalg.solve(self.dense_K(variant), b)
         else:
             D = np.ones((self.nx, 4))
-            if variant not in ("std", "p0") and precond in ("jacobi", "dsa"):
+            if variant not in ("std", "p0") and precond in ("jacobi", "dsa", "vdsa"):
                 D[:, 1:] = self.B11mat().diagonal().reshape(self.nx, 3)
-            if precond == "dsa":
+            if precond == "vdsa":
+                from oracle.vdsa import VertexCorrection
+                Minv = VertexCorrection(self.p, variant, None if variant == "std" else D[:, 1:], cycles=dsa_cycles,
+                                        **(mg or {}))
+            elif precond == "dsa":
                 from oracle.dsa import DiffusionCorrection
                 corr = DiffusionCorrection(self.p, cycles=dsa_cycles)
                 Minv = lambda v: corr(v) / D.ravel()
@@ -476,7 +483,7 @@ class SweepOracle:
             op = spla.LinearOperator((n4, n4), matvec=lambda v: self.K(variant, Minv(v)).ravel(),
                                      dtype=np.float64)
             cnt = [0]
-            if x0 is not None and precond == "dsa":
+            if x0 is not None and precond in ("dsa", "vdsa"):
                 raise ValueError("an initial guess is not supported with the diffusion correction")
             y0 = None if x0 is None else x0.ravel() * (1.0 if precond != "jacobi" else D.ravel())
             Y, ierr = spla.gmres(op, b, x0=y0, rtol=tol, atol=0.0, restart=restart, maxiter=maxiter,
@@ -512,12 +519,12 @@ def _b11_sparse(so):
     """B11 as a sparse matrix, assembled by probing the matrix-free B11 apply: cells of equal colour
     (i + 2 j) mod 5 share no stencil neighbourhood, so 5 colours x 3 slope components recover every entry."""
     import scipy.sparse as sp
-    n, nx = so.n, so.nx
+    n, m, nx = so.n, so.m, so.nx
     jj, ii = np.divmod(np.arange(nx), n)
     col = (ii + 2 * jj) % 5
     nbrs = [np.arange(nx)]
     for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
-        ok = (ii + di >= 0) & (ii + di < n) & (jj + dj >= 0) & (jj + dj < n)
+        ok = (ii + di >= 0) & (ii + di < n) & (jj + dj >= 0) & (jj + dj < m)
         nbrs.append(np.where(ok, (jj + dj) * n + ii + di, -1))
     rows, cols, vals = [], [], []
     for c in range(5):

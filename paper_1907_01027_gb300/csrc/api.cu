@@ -67,7 +67,7 @@ int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
   if (c->f2_ready) return 0;
   const size_t na = c->nang, nx = c->nx;
   const size_t nq = c->q_layout == 2 ? na * nx * 4 : nx * 4;
-  const size_t nal = c->has_alpha ? na * 4 * (size_t)c->n * 2 : 0;
+  const size_t nal = c->has_alpha ? na * 2 * (size_t)(c->ni + c->nj) * 2 : 0;
   const size_t ntab = c->coef ? (size_t)c->nmat * c->ncls * c->ncoef : 0;
   struct Item { const double *src; f2 **dst; size_t n; } items[] = {
       {c->d64.ox, &c->d2.ox, na}, {c->d64.oy, &c->d2.oy, na}, {c->d64.w, &c->d2.w, na},
@@ -95,7 +95,7 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     if (store) return LMDG_ERR_ARG;   // float-float sweeps feed residuals only
     if (int e = ensure_f2(c, s)) return e;
   }
-  a.n = c->n; a.nq = c->nq; a.nang = c->nang; a.nx = c->nx;
+  a.ni = c->ni; a.nj = c->nj; a.nq = c->nq; a.nang = c->nang; a.nx = c->nx;
   a.h = (T)c->h; a.eps = (T)c->eps;
   a.g = P == 0 ? c->g64 : (P == 1 ? c->g32 : c->g2);
   if constexpr (P == 0) { a.pd = c->d64; a.p1ra = c->p1ra64; }
@@ -257,6 +257,16 @@ int norm2(lmdg_ctx *c, const double *v, double *out_h, cudaStream_t s) {
   return 0;
 }
 
+// y = Minv x: the right preconditioner of GMRES -- diag(I, diag(B11))^-1 for the low-memory schemes (precond >= 1),
+// then with precond = 2 the vertex diffusion correction y += I_h D_a^-1 R_h (sigma_s/eps) y (one V-cycle)
+int apply_minv(lmdg_ctx *c, double *y, const double *x, cudaStream_t s) {
+  const bool lowmem = c->variant == LMDG_LM || c->variant == LMDG_RLM;
+  const int pmode = (lowmem && c->opt.precond) ? 1 : 0;
+  CK(precond(y, x, c->b11dinv, c->nx, pmode, s));
+  if (c->opt.precond == 2) CK(dsa_apply(c->dsa, c->ni, c->nj, c->h, c->d64.sse, lowmem ? 1 : 0, y, s));
+  return 0;
+}
+
 struct GmresOut {
   int iters = 0;
   double est = 0;
@@ -274,7 +284,6 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   double *hdev = c->red + mdot_partial_len(c->red_len);          // [m+2]
   double *h2dev = hdev + (m + 2);
   double *ydev = h2dev + (m + 2);
-  const int pmode = ((c->variant == LMDG_LM || c->variant == LMDG_RLM) && c->opt.precond) ? 1 : 0;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
   g[0] = rnorm;
   CK(axpby(V, 1.0 / rnorm, r, 0.0, N, s));
@@ -282,7 +291,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   go->breakdown = false;
   for (int j = 0; j < m && j < max_it; ++j) {
     double *vj = V + (size_t)j * N;
-    CK(precond(z, vj, c->b11dinv, c->nx, pmode, s));
+    if (int e = apply_minv(c, z, vj, s)) return e;
     if (int e = sweep_prec(c, fp32, z, w, 0, false, 0, s)) return e;
     // classical Gram-Schmidt, twice in FP64 solves; once in the FP32 inner cycles of the refinement, whose
     // operator is exact to FP32 only and whose target (inner_tol, 1e-4) lies far above the orthogonality a
@@ -335,7 +344,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
   CK(cudaMemcpyAsync(ydev, c->red_h, sizeof(double) * k, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
   CK(maxpy(z, V, N, k, ydev, N, s));
-  CK(precond(d, z, c->b11dinv, c->nx, pmode, s));
+  if (int e = apply_minv(c, d, z, s)) return e;
   CK(cudaStreamSynchronize(s));
   go->iters = k;
   return 0;
@@ -378,9 +387,10 @@ const char *lmdg_strerror(int code) {
   }
 }
 
-int lmdg_info(const lmdg_ctx *c, int *n, int *nang, int *variant) {
+int lmdg_info(const lmdg_ctx *c, int *nx, int *ny, int *nang, int *variant) {
   if (!c) return LMDG_ERR_ARG;
-  if (n) *n = c->n;
+  if (nx) *nx = c->ni;
+  if (ny) *ny = c->nj;
   if (nang) *nang = c->nang;
   if (variant) *variant = c->variant;
   return 0;
@@ -400,6 +410,7 @@ void lmdg_destroy(lmdg_ctx *c) {
   cudaFree(c->cellsrc); cudaFree(c->cellsh);
   cudaFree(c->rev); cudaFree(c->qadj64); cudaFree(c->qadj32); cudaFree(c->adj_buf);
   cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh); cudaFree(c->coef); cudaFree(c->supp);
+  lmdg::dsa_free(c->dsa);
   cudaFree(c->V);
   for (auto &v : c->vec) cudaFree(v);
   cudaFree(c->red);
@@ -412,12 +423,16 @@ void lmdg_destroy(lmdg_ctx *c) {
 }
 
 int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad, const double *sigma_s,
-               const double *sigma_a, const double *q, int q_layout, const double *alpha, double eps,
-               int variant, const lmdg_options *opt) {
+               const double *sigma_a, const double *q, int q_layout, const double *alpha, int alpha_layout,
+               double eps, int variant, const lmdg_options *opt) {
   if (!out || !mesh || !quad || !sigma_s || !sigma_a || !q) return LMDG_ERR_ARG;
   *out = nullptr;
-  const int n = mesh->n;
-  if (n < 1 || n > 65536 || !(mesh->h > 0) || !std::isfinite(mesh->h)) return LMDG_ERR_ARG;
+  const int ni = mesh->nx, nj = mesh->ny;
+  if (ni < 1 || nj < 1 || ni > 65536 || nj > 65536 || (long long)ni * nj > (1LL << 30) || !(mesh->h > 0) ||
+      !std::isfinite(mesh->h))
+    return LMDG_ERR_ARG;
+  if (alpha && alpha_layout != 0 && alpha_layout != 1) return LMDG_ERR_ARG;
+  if (alpha && alpha_layout == 0 && !std::isfinite(alpha[0])) return LMDG_ERR_ARG;
   if (!(eps > 1e-12) || !std::isfinite(eps)) return LMDG_ERR_ARG;
   if (variant < LMDG_STD || variant > LMDG_P0 || q_layout < 0 || q_layout > 2) return LMDG_ERR_ARG;
   const int na = quad->n;
@@ -433,7 +448,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   }
   if (std::fabs(wsum - 1.0) > 1e-12) return LMDG_ERR_QUAD;
   if (cnt[0] != na / 4 || cnt[1] != na / 4 || cnt[2] != na / 4 || cnt[3] != na / 4) return LMDG_ERR_QUAD;
-  const size_t nx = (size_t)n * n;
+  const size_t nx = (size_t)ni * nj;
   for (size_t K = 0; K < nx; ++K) {
     const double ss = sigma_s[K], sa = sigma_a[K];
     if (!(ss >= 0) || !(sa >= 0) || !std::isfinite(ss) || !std::isfinite(sa) || !(ss / eps + eps * sa > 0))
@@ -445,7 +460,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
       (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || (o.recon != 0 && o.recon != 1) ||
       (o.recon && (variant != LMDG_RLM || o.suppress)) ||
-      (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2))
+      (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2) || o.precond < 0 || o.precond > 2 ||
+      (o.precond == 2 && variant == LMDG_P0))
     return LMDG_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
@@ -453,7 +469,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
 
   lmdg_ctx *c = new (std::nothrow) lmdg_ctx();
   if (!c) return LMDG_ERR_NOMEM;
-  c->n = n; c->nx = (int)nx; c->nang = na; c->nq = na / 4; c->variant = variant; c->q_layout = q_layout;
+  c->ni = ni; c->nj = nj; c->nx = (int)nx; c->nang = na; c->nq = na / 4; c->variant = variant; c->q_layout = q_layout;
   c->kvar = variant == LMDG_P0 ? kP0 : ((variant == LMDG_RLM && o.recon) ? kRlmStar : variant);
   c->has_alpha = alpha != nullptr; c->dev = o.device; c->h = mesh->h; c->eps = eps;
   c->x0 = mesh->x0; c->y0 = mesh->y0; c->opt = o;
@@ -484,9 +500,17 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   }
   const double *qsrc = q_layout == 1 ? q : qv.data();
   const size_t qn = q_layout == 1 ? nx * 4 : qv.size();
+  // inflow data per direction: [2 nj + 2 ni][2] (west and east faces by row, south and north faces by column);
+  // alpha_layout 0 expands the single value given to every face and direction (a0 = value, a1 = 0)
+  const size_t per = (size_t)2 * (ni + nj) * 2;
+  std::vector<double> afull;
+  if (alpha && alpha_layout == 0) {
+    afull.assign((size_t)na * per, 0.0);
+    for (size_t f = 0; f < afull.size(); f += 2) afull[f] = alpha[0];
+    alpha = afull.data();
+  }
   std::vector<double> av;
   if (alpha) {
-    const size_t per = (size_t)4 * n * 2;
     av.resize((size_t)na * per);
     for (int k = 0; k < na; ++k) std::memcpy(&av[(size_t)k * per], alpha + (size_t)perm[k] * per, sizeof(double) * per);
   }
@@ -511,20 +535,20 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     Ay[b > 0 ? 0 : 1] += wl * std::fabs(b);
     if (!alpha) continue;
     const double sx = a > 0 ? 1 : -1, sy = b > 0 ? 1 : -1, aa = std::fabs(a), bb = std::fabs(b);
-    const double *al = alpha + (size_t)l * 4 * n * 2;
-    const int i0 = a > 0 ? 0 : n - 1, sidex = a > 0 ? 0 : 1;
-    for (int j = 0; j < n; ++j) {
-      const size_t K = (size_t)j * n + i0;
-      const double a0 = al[((size_t)sidex * n + j) * 2], a1 = al[((size_t)sidex * n + j) * 2 + 1];
+    const double *al = alpha + (size_t)l * per;
+    const int i0 = a > 0 ? 0 : ni - 1, offx = a > 0 ? 0 : nj;           // west / east faces
+    for (int j = 0; j < nj; ++j) {
+      const size_t K = (size_t)j * ni + i0;
+      const double a0 = al[((size_t)offx + j) * 2], a1 = al[((size_t)offx + j) * 2 + 1];
       sq1[3 * K + 0] += wl * (-sx * aa * h * a0);
       sq1[3 * K + 1] += wl * (aa * h / 3.0 * a1);
       sq1[3 * K + 2] += wl * (-sx * aa * h / 3.0 * a1);
       p1ra[2 * K + 0] += wl * sx * (-a0);
     }
-    const int j0 = b > 0 ? 0 : n - 1, sidey = b > 0 ? 2 : 3;
-    for (int i = 0; i < n; ++i) {
-      const size_t K = (size_t)j0 * n + i;
-      const double a0 = al[((size_t)sidey * n + i) * 2], a1 = al[((size_t)sidey * n + i) * 2 + 1];
+    const int j0 = b > 0 ? 0 : nj - 1, offy = 2 * nj + (b > 0 ? 0 : ni);   // south / north faces
+    for (int i = 0; i < ni; ++i) {
+      const size_t K = (size_t)j0 * ni + i;
+      const double a0 = al[((size_t)offy + i) * 2], a1 = al[((size_t)offy + i) * 2 + 1];
       sq1[3 * K + 0] += wl * (bb * h / 3.0 * a1);
       sq1[3 * K + 1] += wl * (-sy * bb * h * a0);
       sq1[3 * K + 2] += wl * (-sy * bb * h / 3.0 * a1);
@@ -579,34 +603,34 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (o.suppress) {
     // interior faces across which (sigma_s, sigma_a) changes: no RLMDG reconstruction there
     std::vector<double> bits(nx, 0.0);
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i) {
-        const size_t K = (size_t)j * n + i;
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        const size_t K = (size_t)j * ni + i;
         unsigned m = 0;
-        const int ni[4] = {i - 1, i + 1, i, i}, nj[4] = {j, j, j - 1, j + 1};
+        const int fi[4] = {i - 1, i + 1, i, i}, fj[4] = {j, j, j - 1, j + 1};
         for (int f = 0; f < 4; ++f) {
-          if (ni[f] < 0 || ni[f] >= n || nj[f] < 0 || nj[f] >= n) continue;
-          const size_t Kn = (size_t)nj[f] * n + ni[f];
+          if (fi[f] < 0 || fi[f] >= ni || fj[f] < 0 || fj[f] >= nj) continue;
+          const size_t Kn = (size_t)fj[f] * ni + fi[f];
           if (sigma_s[Kn] != sigma_s[K] || sigma_a[Kn] != sigma_a[K]) m |= 1u << f;
         }
         bits[K] = m;
       }
     if ((e = upload(&c->supp, bits))) return fail(e);
   }
-  c->g64 = choose_geom(c->kvar, n, c->nq, 0);
-  c->g32 = choose_geom(c->kvar, n, c->nq, 1);
-  c->g2 = choose_geom(c->kvar, n, c->nq, 2);
+  c->g64 = choose_geom(c->kvar, nj, c->nq, 0);
+  c->g32 = choose_geom(c->kvar, nj, c->nq, 1);
+  c->g2 = choose_geom(c->kvar, nj, c->nq, 2);
   if (c->g64.units() == 0 || c->g32.units() == 0 || c->g2.units() == 0) return fail(LMDG_ERR_CUDA);
   if (std::getenv("LMDG_VERBOSE"))
-    std::fprintf(stderr, "lmdg: n=%d n_omega=%d variant=%d fp64 shape groups=%d warps=%d apw=%d | fp32 groups=%d "
-                 "warps=%d apw=%d | f32x2 groups=%d warps=%d apw=%d\n", n, na, variant, c->g64.groups,
+    std::fprintf(stderr, "lmdg: %dx%d cells n_omega=%d variant=%d fp64 shape groups=%d warps=%d apw=%d | fp32 "
+                 "groups=%d warps=%d apw=%d | f32x2 groups=%d warps=%d apw=%d\n", ni, nj, na, variant, c->g64.groups,
                  c->g64.warps, c->g64.apw, c->g32.groups, c->g32.warps, c->g32.apw, c->g2.groups, c->g2.warps,
                  c->g2.apw);
   const size_t pe =
       std::max({part_elems(c->g64, c->nx), part_elems(c->g32, c->nx), part_elems(c->g2, c->nx)});
   if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
-  const int strips = (n + 31) / 32;
-  const size_t ytr_elems = (size_t)na * strips * n * kTraceStride;
+  const int strips = (nj + 31) / 32;
+  const size_t ytr_elems = (size_t)na * strips * ni * kTraceStride;
   if (cudaMalloc(&c->ytr, sizeof(double) * ytr_elems) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   c->ytr_words = 2 * ytr_elems;
   c->ytr_dirty = true;
@@ -664,6 +688,13 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       c->coef = nullptr; c->mat = nullptr; c->cls = nullptr; c->matsh = nullptr;
     }
   }
+  if (o.precond == 2) {
+    // vertex diffusion correction of the scheme's own diffusion limit (full gradient for Q1-DG, cell-averaged
+    // gradient for the low-memory schemes), multigrid hierarchy built on the device
+    if (int e2 = dsa_build(c->dsa, variant == LMDG_STD ? 0 : 1, ni, nj, h, eps, c->d64.sigt, c->sigma_a, Ax[0], Ay[0],
+                           0))
+      return fail(e2);
+  }
   *out = c;
   return 0;
 }
@@ -683,7 +714,9 @@ int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream)
     yd = c->vec[5];
   }
   const int prec = (flags & LMDG_SWEEP_FP32) ? 1 : ((flags & LMDG_SWEEP_F32X2) ? 2 : 0);
-  if (int e = sweep_prec(c, prec, xd, yd, (flags & LMDG_SWEEP_SOURCE) ? 1 : 0, (flags & LMDG_SWEEP_STORE) != 0, 0,
+  // FP32 storing sweeps of an LMDG_FP32_BF16STORE context keep the low-memory unknowns in bfloat16
+  const int bf16 = (prec == 1 && c->opt.precision == LMDG_FP32_BF16STORE) ? 1 : 0;
+  if (int e = sweep_prec(c, prec, xd, yd, (flags & LMDG_SWEEP_SOURCE) ? 1 : 0, (flags & LMDG_SWEEP_STORE) != 0, bf16,
                          s))
     return e;
   if (flags & LMDG_HOST_PTRS) CK(cudaMemcpyAsync(y, yd, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -699,13 +732,13 @@ int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   if (flags & LMDG_HOST_PTRS) {
     double *tmp = nullptr;
     if (cudaMalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
-    cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->n, c->psi_elems, s);
+    cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s);
     cudaError_t e2 = cudaMemcpyAsync(psi, tmp, sizeof(double) * c->psi_elems, cudaMemcpyDeviceToHost, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
     cudaFree(tmp);
     return (e1 || e2 || e3) ? LMDG_ERR_CUDA : 0;
   }
-  CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->n, c->psi_elems, s));
+  CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s));
   return 0;
 }
 
@@ -823,12 +856,12 @@ int lmdg_b11_apply(lmdg_ctx *c, const double *x, double *y, int flags, void *str
   if (flags & LMDG_HOST_PTRS) {
     if (int e = ensure_krylov(c, c->opt.restart)) return e;
     CK(cudaMemcpyAsync(c->vec[4], x, sizeof(double) * N3, cudaMemcpyHostToDevice, s));
-    CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, c->vec[4], c->vec[5], s));
+    CK(b11_apply(c->ni, c->nj, c->h, c->eps, c->sigma_a, A4, c->vec[4], c->vec[5], s));
     CK(cudaMemcpyAsync(y, c->vec[5], sizeof(double) * N3, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return 0;
   }
-  CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, x, y, s));
+  CK(b11_apply(c->ni, c->nj, c->h, c->eps, c->sigma_a, A4, x, y, s));
   return 0;
 }
 
@@ -858,7 +891,7 @@ int lmdg_b11_solve(lmdg_ctx *c, const double *r, double *z, double tol, int *ite
   int it = 0;
   const int maxit = 100000;
   while (rr > stop && it < maxit) {
-    CK(b11_apply(c->n, c->h, c->eps, c->sigma_a, A4, Pp, Ap, s));
+    CK(b11_apply(c->ni, c->nj, c->h, c->eps, c->sigma_a, A4, Pp, Ap, s));
     double pap = 0;
     if (int e = dot(Pp, Ap, &pap)) return e;
     if (!(pap > 0)) return LMDG_ERR_BREAKDOWN;
@@ -876,6 +909,22 @@ int lmdg_b11_solve(lmdg_ctx *c, const double *r, double *z, double tol, int *ite
                      (flags & LMDG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   return rr > stop ? LMDG_ERR_NOTCONV : 0;
+}
+
+int lmdg_precond_apply(lmdg_ctx *c, const double *x, double *y, int flags, void *stream) {
+  if (!c || !x || !y) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const size_t N = 4 * (size_t)c->nx;
+  if (flags & LMDG_HOST_PTRS) {
+    if (int e = ensure_krylov(c, c->opt.restart)) return e;
+    CK(cudaMemcpyAsync(c->vec[4], x, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    if (int e = apply_minv(c, c->vec[5], c->vec[4], s)) return e;
+    CK(cudaMemcpyAsync(y, c->vec[5], sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+  }
+  return apply_minv(c, y, x, s);
 }
 
 int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double *dq, double *J, lmdg_stats *st,

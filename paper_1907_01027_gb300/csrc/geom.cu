@@ -6,12 +6,12 @@
 
 namespace lmdg {
 
-SweepGeom env_override(SweepGeom best, int nq, int n, int amax) {
+SweepGeom env_override(SweepGeom best, int nq, int nj, int amax) {
   if (const char *e = std::getenv("LMDG_SWEEP_GEOM")) {
     int a = 0, b = 0, c = 0;
     if (std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a >= 1 && a <= nq && b >= 1 && b <= 8 && c >= 1 &&
         c <= amax && b * c >= (nq + a - 1) / a && (a - 1) * ((nq + a - 1) / a) < nq)
-      best = SweepGeom{a, b, c, (n + 31) / 32};
+      best = SweepGeom{a, b, c, (nj + 31) / 32};
   }
   return best;
 }
@@ -29,7 +29,7 @@ SweepGeom env_override(SweepGeom best, int nq, int n, int amax) {
 //         compiled): Q1-DG one direction per warp, 4 warps (4.45 against 4.68 with 8 warps); LMDG and P0-DG two
 //         directions per warp, 4 warps (3.18 against 3.29 with 2 warps); RLMDG one direction per warp, 8 warps
 //         (5.32 against 5.96 with two directions and 6 warps).
-SweepGeom choose_geom(int variant, int n, int nq, int prec) {
+SweepGeom choose_geom(int variant, int nj, int nq, int prec) {
   int apw, wmax;
   if (prec == 0) { apw = variant == LMDG_STD ? 1 : 2; wmax = variant == LMDG_STD ? 4 : 3; }
   else if (prec == 2) {
@@ -42,7 +42,7 @@ SweepGeom choose_geom(int variant, int n, int nq, int prec) {
   const int gsize = (nq + G - 1) / G;
   const int a = gsize < apw ? gsize : apw;
   const int W = (gsize + a - 1) / a;
-  return env_override(SweepGeom{G, W, a, (n + 31) / 32}, nq, n, prec == 2 ? 2 : kMaxA);
+  return env_override(SweepGeom{G, W, a, (nj + 31) / 32}, nq, nj, prec == 2 ? 2 : kMaxA);
 }
 
 }  // namespace lmdg

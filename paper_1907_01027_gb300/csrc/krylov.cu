@@ -142,12 +142,12 @@ __global__ void precond_kernel(double *__restrict__ y, const double *__restrict_
 // slope basis (xi, eta, xi eta), with s = +-1 the side of the face:
 //   x-face (xi = s): traces (s, eta, s eta): int b_r b_q ds = h [[1,0,0],[0,1/3,s/3],[0,s/3,1/3]] with the
 //   neighbour's trace (-s, eta, -s eta) entering as h [[-1,0,0],[0,1/3,-s/3],[0,s/3,-1/3]]  (rows own, cols nbr)
-__global__ void b11_kernel(int n, double h, double eps, const double *__restrict__ sigma_a, double Axp,
+__global__ void b11_kernel(int ni, int nj, double h, double eps, const double *__restrict__ sigma_a, double Axp,
                            double Axm, double Ayp, double Aym, const double *__restrict__ u,
                            double *__restrict__ y) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= n * n) return;
-  const int i = K % n, j = K / n;
+  if (K >= ni * nj) return;
+  const int i = K % ni, j = K / ni;
   const double *uk = u + 3 * (size_t)K;
   const double c1 = uk[0], c2 = uk[1], c3 = uk[2];
   const double m = eps * sigma_a[K] * h * h;
@@ -162,8 +162,8 @@ __global__ void b11_kernel(int n, double h, double eps, const double *__restrict
     y1 += wo * h * (s * o0);
     y2 += wo * h * (o1 / 3.0);
     y3 += wo * h * (s * o1 / 3.0);
-    if (in >= 0 && in < n) {
-      const double *un = u + 3 * (size_t)(j * n + in);
+    if (in >= 0 && in < ni) {
+      const double *un = u + 3 * (size_t)(j * ni + in);
       // neighbour trace on the shared face (its xi = -s): (-s n1) + (n2 - s n3) eta
       const double e0 = -s * un[0], e1 = un[1] - s * un[2];
       y1 -= wi * h * (s * e0);
@@ -180,8 +180,8 @@ __global__ void b11_kernel(int n, double h, double eps, const double *__restrict
     y1 += wo * h * (o1 / 3.0);
     y2 += wo * h * (s * o0);
     y3 += wo * h * (s * o1 / 3.0);
-    if (jn >= 0 && jn < n) {
-      const double *un = u + 3 * (size_t)(jn * n + i);
+    if (jn >= 0 && jn < nj) {
+      const double *un = u + 3 * (size_t)(jn * ni + i);
       const double e0 = -s * un[1], e1 = un[0] - s * un[2];
       y1 -= wi * h * (e1 / 3.0);
       y2 -= wi * h * (s * e0);
@@ -239,14 +239,14 @@ __global__ void fill_u32_kernel(unsigned *__restrict__ p, unsigned v, size_t N) 
 
 // Stored angular unknowns to the user layout: the sweeps keep them column-major per direction, [u][i][j][per]
 // (a warp's 32 rows of one column contiguous); the user layout is row-major, [u][j][i][per], in double.
-__global__ void psi_to_user_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, int per, int n,
-                                   size_t N) {
-  const size_t nx = (size_t)n * n;
+__global__ void psi_to_user_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, int per, int ni,
+                                   int nj, size_t N) {
+  const size_t nx = (size_t)ni * nj;
   for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < N; o += (size_t)gridDim.x * blockDim.x) {
     const size_t c = o % per, cell = o / per;
     const size_t u = cell / nx, K = cell - u * nx;
-    const size_t j = K / n, i = K - j * n;
-    const size_t k = (u * nx + i * n + j) * per + c;
+    const size_t j = K / ni, i = K - j * ni;
+    const size_t k = (u * nx + i * nj + j) * per + c;
     if (kind == 1) y[o] = (double)reinterpret_cast<const float *>(x)[k];
     else if (kind == 2) y[o] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
     else y[o] = reinterpret_cast<const double *>(x)[k];
@@ -300,10 +300,10 @@ cudaError_t precond(double *y, const double *x, const double *dinv, int nx, int 
   precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, dinv, nx, mode);
   return cudaGetLastError();
 }
-cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
+cudaError_t b11_apply(int ni, int nj, double h, double eps, const double *sigma_a, const double *A4, const double *u,
                       double *y, cudaStream_t s) {
   add_launches(1);
-  b11_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
+  b11_kernel<<<(ni * nj + 255) / 256, 256, 0, s>>>(ni, nj, h, eps, sigma_a, A4[0], A4[1], A4[2], A4[3], u, y);
   return cudaGetLastError();
 }
 cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, const double *part,
@@ -318,9 +318,9 @@ cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s) {
   fill_u32_kernel<<<grid_for(N), 256, 0, s>>>(p, v, N);
   return cudaGetLastError();
 }
-cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int n, size_t N, cudaStream_t s) {
+cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int ni, int nj, size_t N, cudaStream_t s) {
   add_launches(1);
-  psi_to_user_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, per, n, N);
+  psi_to_user_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, per, ni, nj, N);
   return cudaGetLastError();
 }
 

@@ -16,8 +16,8 @@ cudaError_t scale_by_inv(double *y, const double *x, const double *nrm2, size_t 
 cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cudaStream_t s);
 // y = diag(I, 1/dinv)^-1 x on [nx][4] (mode 1) or y = x (mode 0); dinv = reciprocal diagonal
 cudaError_t precond(double *y, const double *x, const double *dinv, int nx, int mode, cudaStream_t s);
-// y = B11 u on [nx][3]; A4 = {Ax+, Ax-, Ay+, Ay-}
-cudaError_t b11_apply(int n, double h, double eps, const double *sigma_a, const double *A4, const double *u,
+// y = B11 u on [nx][3] (ni x nj cells); A4 = {Ax+, Ax-, Ay+, Ay-}
+cudaError_t b11_apply(int ni, int nj, double h, double eps, const double *sigma_a, const double *A4, const double *u,
                       double *y, cudaStream_t s);
 // out[0..nx) = dJ/dsigma_s, out[nx..2nx) = dJ/dsigma_a, out[2nx..3nx) = dJ/dq; Phi, Lam: forward and adjoint
 // reduced solutions (standard) or scalar-flux moments (low-memory)
@@ -26,6 +26,6 @@ cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, 
 // p[0..N) = v
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s);
 // stored psi (column-major per direction, kind 0 double, 1 float, 2 bfloat16; per values per cell) to the user
-// layout [u][n*n][per] in double; N = directions * n * n * per
-cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int n, size_t N, cudaStream_t s);
+// layout [u][nj*ni][per] in double; N = directions * ni * nj * per
+cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int ni, int nj, size_t N, cudaStream_t s);
 }  // namespace lmdg

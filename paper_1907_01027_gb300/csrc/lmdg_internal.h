@@ -16,7 +16,8 @@ struct ProblemData {
   T *sigt = nullptr;                              // [nx] sigma_s/eps + eps sigma_a
   T *sse = nullptr;                               // [nx] sigma_s/eps
   T *q = nullptr;                                 // [nx][4] or [nang(sorted)][nx][4]
-  T *alpha = nullptr;                             // [nang(sorted)][4][n][2] or null
+  T *alpha = nullptr;                             // [nang(sorted)][2 nj + 2 ni][2] or null (faces: west, east,
+                                                  // south, north)
 };
 
 // Sweep launch geometry: one CTA per (quadrant, angle group, strip of 32 rows); warps of a CTA hold
@@ -25,7 +26,7 @@ struct SweepGeom {
   int groups;      // angle groups per quadrant
   int warps;       // warps per CTA
   int apw;         // angles per warp (<= kMaxA)
-  int strips;      // ceil(n / 32)
+  int strips;      // ceil(nj / 32): strips of 32 rows
   int units() const { return 4 * groups * strips; }
 };
 
@@ -42,7 +43,7 @@ constexpr int kP0 = 4;               // kernel variant of P0-DG (LMDG_P0)
 // Arguments of one sweep launch (everything a kernel reads or writes).
 template <typename T>
 struct SweepArgs {
-  int n, nq, nang, nx;
+  int ni, nj, nq, nang, nx;   // cells along x, along y; directions per quadrant, directions; cells
   T h, eps;
   SweepGeom g;
   ProblemData<T> pd;
@@ -51,11 +52,11 @@ struct SweepArgs {
   const T *p1ra;       // [nx][2] P1 r_alpha (RLMDG, source sweeps) or null
   int source;          // 1: add eps q and the inflow data alpha
   T *part;             // [4*groups][nx][NR] partial reductions, written once each
-  void *psi;           // storing sweep output or null: [nang (user order, through perm)][n (column i)][n (row j)]
+  void *psi;           // storing sweep output or null: [nang (user order, through perm)][ni (column i)][nj (row j)]
                        // [4 standard, 1 low-memory], column-major cells so that a warp's stores coalesce
   int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
   const int *perm;     // [nang] sorted index -> user index
-  T *ytr;              // [nang][strips][n][kTraceStride] strip-boundary traces, kTraceEmpty when unwritten
+  T *ytr;              // [nang][strips][ni][kTraceStride] strip-boundary traces, kTraceEmpty when unwritten
   unsigned *ctrl;      // [0] ticket, [1] error
   long long spin_limit;
   const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
@@ -73,6 +74,34 @@ struct SweepArgs {
   const int *mat;      // [nx] material of each cell (prep_kernel writes it into the cellsh slot)
   const unsigned *supp;  // RLMDG: [nx] faces without reconstruction (1 west, 2 east, 4 south, 8 north) or null
 };
+
+// Vertex diffusion correction (dsa.cu): one multigrid level, nine-point stencils of bs x bs blocks on the
+// (ni + 1) x (nj + 1) vertices of ni x nj cells, with its block-diagonal inverse and work vectors.
+struct MgLevel {
+  int ni = 0, nj = 0, bs = 1;
+  double *A = nullptr;     // [vertices][9][bs][bs]
+  double *dinv = nullptr;  // [vertices][bs][bs]
+  double *x = nullptr, *y = nullptr, *b = nullptr, *r = nullptr;   // [vertices][bs]
+};
+constexpr int kMaxMgLevels = 24;
+constexpr int kMaxDense = 1156;   // largest coarsest level solved with a dense inverse (unknowns)
+struct VertexDsa {
+  int avg = 0;                     // 1: cell-average gradient (low-memory schemes), 0: full gradient (Q1-DG)
+  int nlev = -1;                   // levels with a coarser one below; lev[nlev] is the coarsest (-1: not built)
+  MgLevel lev[kMaxMgLevels];
+  double *cinv = nullptr;          // dense inverse of the coarsest matrix, or null (then coarse_sweeps Jacobi steps)
+  int nu = 2, coarse_sweeps = 50;  // smoothing steps before and after the coarse correction; coarsest fallback
+  double omega = 0.7;              // damping of the block-Jacobi smoother
+};
+// Build the hierarchy for ni x nj cells (sigt, sigma_a per cell, device; Ax, Ay the half-range outflow weights):
+// 0 or an LMDG_ERR_* code.  Synchronises s.
+int dsa_build(VertexDsa &d, int avg, int ni, int nj, double h, double eps, const double *sigt, const double *sigma_a,
+              double Ax, double Ay, cudaStream_t s);
+void dsa_free(VertexDsa &d);
+// u += I_h D_a^-1 R_h (sigma_s/eps) u~ with one V-cycle, u [ni*nj][4]; lowmem: u holds (X0, X1) and the
+// scalar-flux slopes are -X1 (u~ = (u0, -u1), correction (c0, -c1))
+cudaError_t dsa_apply(const VertexDsa &d, int ni, int nj, double h, const double *sse, int lowmem, double *u,
+                      cudaStream_t s);
 
 // Number of kernels launched by this library (all host wrappers add to it).
 long long launch_count();
@@ -94,8 +123,8 @@ int sweep_blocks_per_sm(int variant, int warps, int apw);
 template <typename T>
 constexpr int prec_of() { return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2); }
 
-// launch shape for a problem and sweep arithmetic prec; LMDG_SWEEP_GEOM="groups,warps,apw" overrides
-SweepGeom choose_geom(int variant, int n, int nq, int prec);
+// launch shape for nj rows and sweep arithmetic prec; LMDG_SWEEP_GEOM="groups,warps,apw" overrides
+SweepGeom choose_geom(int variant, int nj, int nq, int prec);
 // y[i] = x[i] rounded to float-float
 cudaError_t convert_to_f2(const double *x, f2 *y, size_t n, cudaStream_t s);
 
@@ -112,7 +141,7 @@ cudaError_t quad_moments(int nang, const double *ox, const double *oy, const dou
 
 // Context
 struct lmdg_ctx {
-  int n = 0, nx = 0, nang = 0, nq = 0, variant = 0, q_layout = 0, has_alpha = 0, dev = 0;
+  int ni = 0, nj = 0, nx = 0, nang = 0, nq = 0, variant = 0, q_layout = 0, has_alpha = 0, dev = 0;
   int kvar = 0;                            // kernel variant: the scheme, kRlmStar for RLMDG*, kP0 for P0-DG
   double h = 0, eps = 0, x0 = 0, y0 = 0;
   lmdg_options opt{};
@@ -173,4 +202,5 @@ struct lmdg_ctx {
   double *coef = nullptr;                  // [nmat][ncls][ncoef]
   lmdg::f2 *coef2 = nullptr;               // the same, float-float
   unsigned *supp = nullptr;                // RLMDG suppression bits per cell, or null
+  lmdg::VertexDsa dsa;                     // vertex diffusion correction (precond = 2)
 };

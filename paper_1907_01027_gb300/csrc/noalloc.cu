@@ -129,7 +129,7 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   }
 
   SweepArgs<double> a{};
-  a.n = n; a.nq = nq; a.nang = n_omega; a.nx = (int)nx;
+  a.ni = n; a.nj = n; a.nq = nq; a.nang = n_omega; a.nx = (int)nx;
   a.h = h; a.eps = 1.0;
   a.g = g;
   a.pd.ox = const_cast<double *>(ox);

@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int W = A.g.warps;
-  const int n = A.n, nx = A.nx;
+  const int ni = A.ni, nj = A.nj, nx = A.nx;   // ni columns along x, nj rows along y, nx cells
+  const int nfaces = 2 * (ni + nj);               // inflow data per direction: west, east (nj each), south, north (ni)
   T *red = reinterpret_cast<T *>(smem_raw);          // [2][C][W][32][NR]
   T *cs = red + (size_t)2 * C * W * NR * 32;         // [2][C][32][4]
   T *csh = cs + (size_t)2 * C * 32 * 4;              // [2][C][32]
@@ -465,8 +466,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   const T G3a = flip(Ga, mxy), G3b = flip(Gb, mxy);
 
   const int row = strip * 32 + lane;
-  const bool row_ok = row < n;
-  const int j = sy > 0 ? row : n - 1 - row;
+  const bool row_ok = row < nj;
+  const int j = sy > 0 ? row : nj - 1 - row;
   const T h = A.h;
   const T *tab = TAB ? A.coef : nullptr;
   const int tab_stride = TAB ? A.ncls * NC : 0;
@@ -488,9 +489,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     if (it >= APW * C * NS) return nullptr;
     const int k = it / (C * NS), rem = it - k * C * NS, s = rem / NS, c = rem - s * NS;
     const int x = t0 + s;
-    if (k >= nA || x >= n) return nullptr;
+    if (k >= nA || x >= ni) return nullptr;
     const int ak = quad * A.nq + g0 + min(warp + k * W, gcount - 1);
-    return A.ytr + (((size_t)ak * A.g.strips + (strip - 1)) * n + x) * kTraceStride + c;
+    return A.ytr + (((size_t)ak * A.g.strips + (strip - 1)) * ni + x) * kTraceStride + c;
   };
   T pre[NI];
 #pragma unroll
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       if (p) pre[q] = ld_relaxed_t(p);
     }
   }
-  const int nsteps = n + 31;
+  const int nsteps = ni + 31;
   const int nchunks = (nsteps + C - 1) / C;
 
   // cell data of chunk cc -> buffer cc & 1 (item = (step, lane) of the chunk)
@@ -511,9 +512,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     for (int it = threadIdx.x; it < C * 32; it += blockDim.x) {
       const int s = it >> 5, l = it & 31;
       const int r = strip * 32 + l, x = cc * C + s - l;
-      if (r < n && x >= 0 && x < n) {
-        const int ii = sx > 0 ? x : n - 1 - x, jj = sy > 0 ? r : n - 1 - r;
-        const size_t K = (size_t)jj * n + ii;
+      if (r < nj && x >= 0 && x < ni) {
+        const int ii = sx > 0 ? x : ni - 1 - x, jj = sy > 0 ? r : nj - 1 - r;
+        const size_t K = (size_t)jj * ni + ii;
         copy_cell<T>(cs + ((size_t)(b * C + s) * 32 + l) * 4, csh + (size_t)(b * C + s) * 32 + l,
                      A.cellsrc + 4 * K, A.cellsh + K);
         if (VAR == 2 && A.supp) cp_async4(csup + (size_t)(b * C + s) * 32 + l, A.supp + K);
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     // ---- inflow from the strip below: the traces of columns [t0, t0 + C) for this warp's directions
     // (prefetched during the previous chunk), polled until present, staged in shared memory, and consumed
     bool wabort = false;
-    if (strip > 0 && t0 < n) {
+    if (strip > 0 && t0 < ni) {
       int ab = 0;
       T *yw = yup + (size_t)warp * APW * C * NS;
 #pragma unroll
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       wabort = __any_sync(kFull, ab) != 0;
       __syncwarp();
       if (wabort && lane == 0) s_abort = 1;
-      if (!wabort && t0 + C < n) {
+      if (!wabort && t0 + C < ni) {
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
           const T *p = up_addr(lane + 32 * q, t0 + C);
@@ -581,12 +582,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         const int t = t0 + s;
         if (t >= nsteps) break;
         const int x = t - lane;
-        const bool act = row_ok && x >= 0 && x < n;
-        const int i = sx > 0 ? x : n - 1 - x;
-        const int K = act ? j * n + i : 0;
+        const bool act = row_ok && x >= 0 && x < ni;
+        const int i = sx > 0 ? x : ni - 1 - x;
+        const int K = act ? j * ni + i : 0;
         // stored angular unknowns (and the adjoint's correlation input) are column-major, [i][j]: the warp's 32
         // rows of one column are contiguous, so its psi stores coalesce
-        const int Kt = act ? i * n + j : 0;
+        const int Kt = act ? i * nj + j : 0;
         const bool xbnd = (x == 0);
         const bool ybnd = (strip == 0 && lane == 0);
         const T *yws = yup + ((size_t)warp * APW * C + s) * NS;   // + k * C * NS: direction k's inflow (lane 0)
@@ -646,12 +647,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
               T xa0 = 0, xa1 = 0, ya0 = 0, ya1 = 0;
               if (src_bnd) {
                 if (xbnd) {
-                  const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sx > 0 ? 0 : 1)) * n + j) * 2);
+                  const T *ap = A.pd.alpha + ((size_t)ang[k] * nfaces + (sx > 0 ? 0 : nj) + j) * 2;
                   xa0 = ap[0];
                   xa1 = flip(ap[1], my);
                 }
                 if (ybnd) {
-                  const T *ap = A.pd.alpha + ((((size_t)ang[k] * 4 + (sy > 0 ? 2 : 3)) * n + i) * 2);
+                  const T *ap = A.pd.alpha + ((size_t)ang[k] * nfaces + 2 * nj + (sy > 0 ? 0 : ni) + i) * 2;
                   ya0 = ap[0];
                   ya1 = flip(ap[1], mx);
                 }
@@ -807,7 +808,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
-                T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * n + x) * kTraceStride;
+                T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * ni + x) * kTraceStride;
 #pragma unroll
                 for (int c = 0; c < NS; ++c) st_trace(yp + c, ys[k][c]);
               }
@@ -836,9 +837,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     for (int it = threadIdx.x; it < C * 32; it += blockDim.x) {
       const int s = it >> 5, l = it & 31;
       const int t = t0 + s, x = t - l, r = strip * 32 + l;
-      if (t >= nsteps || r >= n || x < 0 || x >= n) continue;
-      const int ii = sx > 0 ? x : n - 1 - x, jj = sy > 0 ? r : n - 1 - r;
-      const size_t K = (size_t)jj * n + ii;
+      if (t >= nsteps || r >= nj || x < 0 || x >= ni) continue;
+      const int ii = sx > 0 ? x : ni - 1 - x, jj = sy > 0 ? r : nj - 1 - r;
+      const size_t K = (size_t)jj * ni + ii;
       T sum[NR];
       load_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W) * 32 + l) * NR);   // warp 0, then the others in order
       for (int ww = 1; ww < W; ++ww) {

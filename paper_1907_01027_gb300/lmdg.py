@@ -25,7 +25,8 @@ class LmdgError(RuntimeError):
 
 
 class Mesh(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double)]
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("h", ctypes.c_double)]
 
 
 class Quad(ctypes.Structure):
@@ -68,14 +69,15 @@ def _lib():
         sig = {
             "lmdg_default_options": ([vp], ip),
             "lmdg_strerror": ([ip], ctypes.c_char_p),
-            "lmdg_setup": ([vp, vp, vp, vp, vp, vp, ip, vp, dp, ip, vp], ip),
+            "lmdg_setup": ([vp, vp, vp, vp, vp, vp, ip, vp, ip, dp, ip, vp], ip),
             "lmdg_sweep": ([vp, vp, vp, ip, vp], ip),
             "lmdg_solve": ([vp, vp, vp, vp, vp, ip, vp], ip),
             "lmdg_get_psi": ([vp, vp, ip, vp], ip),
             "lmdg_adjoint": ([vp, vp, vp, vp, vp, vp, vp, ip, vp], ip),
             "lmdg_b11_apply": ([vp, vp, vp, ip, vp], ip),
             "lmdg_b11_solve": ([vp, vp, vp, dp, vp, ip, vp], ip),
-            "lmdg_info": ([vp, vp, vp, vp], ip),
+            "lmdg_precond_apply": ([vp, vp, vp, ip, vp], ip),
+            "lmdg_info": ([vp, vp, vp, vp, vp], ip),
             "lmdg_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
@@ -108,27 +110,42 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
+def pack_alpha(alpha, ncol, nrow):
+    """Inflow data [n_Omega][4][max(ncol, nrow)][2] (sides west, east: nrow faces; south, north: ncol faces, each
+    in its first entries) to the library's face list [n_Omega][2 nrow + 2 ncol][2]."""
+    a = np.asarray(alpha, dtype=np.float64)
+    return np.ascontiguousarray(np.concatenate([a[:, 0, :nrow], a[:, 1, :nrow], a[:, 2, :ncol], a[:, 3, :ncol]],
+                                               axis=1))
+
+
 class Context:
-    """One problem on one GPU (lmdg_setup ... lmdg_destroy)."""
+    """One problem on one GPU (lmdg_setup ... lmdg_destroy).  The problem's mesh has ``n`` cells along x and
+    ``rows`` along y; a scalar ``alpha`` is the same inflow value on every face and direction."""
 
     def __init__(self, problem, variant, **opts):
         self.lib = _lib()
         p = problem
         self.n, self.nx, self.nang = p.n, p.nx, p.nang
+        self.rows = getattr(p, "rows", p.n)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.ox, p.oy, p.w)]
-        mesh = Mesh(p.n, p.x0, p.y0, p.h)
+        mesh = Mesh(p.n, self.rows, p.x0, p.y0, p.h)
         quad = Quad(p.nang, *[a.ctypes.data for a in self._keep])
         ss = np.ascontiguousarray(p.sigma_s, dtype=np.float64)
         sa = np.ascontiguousarray(p.sigma_a, dtype=np.float64)
         q = np.ascontiguousarray(p.q, dtype=np.float64)
         q_layout = 2 if q.ndim == 3 else 1
-        al = None if p.alpha is None else np.ascontiguousarray(p.alpha, dtype=np.float64)
+        if p.alpha is None:
+            al, al_layout = None, 1
+        elif np.ndim(p.alpha) == 0:
+            al, al_layout = np.array([float(p.alpha)]), 0
+        else:
+            al, al_layout = pack_alpha(p.alpha, p.n, self.rows), 1
         self.options = default_options(**opts)
         h = ctypes.c_void_p()
         rc = self.lib.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ss.ctypes.data,
                                  sa.ctypes.data, q.ctypes.data, q_layout, None if al is None else al.ctypes.data,
-                                 float(p.eps), self.variant, ctypes.byref(self.options))
+                                 al_layout, float(p.eps), self.variant, ctypes.byref(self.options))
         if rc:
             raise LmdgError(rc, "lmdg_setup")
         self.h = h
@@ -191,6 +208,14 @@ class Context:
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.nx, 3)
         y = np.empty_like(x)
         self._check(self.lib.lmdg_b11_apply(self.h, x.ctypes.data, y.ctypes.data, HOST_PTRS, None), "lmdg_b11_apply")
+        return y
+
+    def precond_apply(self, x):
+        """lmdg_precond_apply: y = Minv x, the right preconditioner of lmdg_solve (host arrays)."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.nx, 4)
+        y = np.empty_like(x)
+        self._check(self.lib.lmdg_precond_apply(self.h, x.ctypes.data, y.ctypes.data, HOST_PTRS, None),
+                    "lmdg_precond_apply")
         return y
 
     def b11_solve(self, r, tol=1e-14):

@@ -21,14 +21,14 @@ def _setup(L, p, eps=None, variant=0, ox=None, oy=None, w=None, nang=None):
     ox = np.ascontiguousarray(p.ox if ox is None else ox)
     oy = np.ascontiguousarray(p.oy if oy is None else oy)
     w = np.ascontiguousarray(p.w if w is None else w)
-    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     quad = Quad(len(w) if nang is None else nang, ox.ctypes.data, oy.ctypes.data, w.ctypes.data)
     ss = np.ascontiguousarray(p.sigma_s)
     sa = np.ascontiguousarray(p.sigma_a)
     q = np.ascontiguousarray(p.q)
     h = ctypes.c_void_p()
     rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ss.ctypes.data, sa.ctypes.data,
-                      q.ctypes.data, 1, None, float(p.eps if eps is None else eps), variant, None)
+                      q.ctypes.data, 1, None, 1, float(p.eps if eps is None else eps), variant, None)
     if rc == 0:
         L.lmdg_destroy(h)
     return rc
@@ -72,7 +72,7 @@ def test_suppress_option_validated(L):
     """The suppression switch is RLMDG's only and takes 0 or 1."""
     from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
-    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
     quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
     for variant, flag in ((0, 1), (1, 1), (2, 2), (2, -1)):
@@ -81,7 +81,7 @@ def test_suppress_option_validated(L):
         o.suppress = flag
         h = ctypes.c_void_p()
         rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
-                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1, 1.0, variant, ctypes.byref(o))
         assert rc == -1, (variant, flag)
 
 
@@ -89,7 +89,7 @@ def test_recon_option_validated(L):
     """The three-cell reconstruction (RLMDG*) is RLMDG's only, takes 0 or 1 and excludes suppression."""
     from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
-    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
     quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
     for variant, recon, supp in ((0, 1, 0), (1, 1, 0), (3, 1, 0), (2, 2, 0), (2, 1, 1)):
@@ -99,7 +99,7 @@ def test_recon_option_validated(L):
         o.suppress = supp
         h = ctypes.c_void_p()
         rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
-                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, variant, ctypes.byref(o))
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1, 1.0, variant, ctypes.byref(o))
         assert rc == -1, (variant, recon, supp)
 
 
@@ -107,7 +107,7 @@ def test_resid_option_validated(L):
     """The residual arithmetic takes LMDG_RESID_FP64 (0) or LMDG_RESID_F32X2 (1) only."""
     from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
-    mesh = Mesh(p.n, p.x0, p.y0, p.h)
+    mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
     quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
     for resid in (-1, 2, 7):
@@ -117,5 +117,40 @@ def test_resid_option_validated(L):
         o.resid = resid
         h = ctypes.c_void_p()
         rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
-                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1.0, 0, ctypes.byref(o))
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1, 1.0, 0, ctypes.byref(o))
         assert rc == -1, resid
+
+
+def test_precond_option_validated(L):
+    """The preconditioner takes 0, 1 or 2 (the vertex diffusion correction), and 2 is refused for P0-DG, whose
+    scheme has no diffusion limit."""
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
+    arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
+    quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+    for variant, pc in ((0, -1), (1, 3), (3, 2)):
+        o = Options()
+        L.lmdg_default_options(ctypes.byref(o))
+        assert o.precond == 1
+        o.precond = pc
+        h = ctypes.c_void_p()
+        rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None, 1, 1.0, variant, ctypes.byref(o))
+        assert rc == -1, (variant, pc)
+
+
+def test_mesh_and_alpha_layout_validated(L):
+    """Meshes need at least one cell along each axis; the inflow data layout is 0 (one value) or 1 (per face)."""
+    from paper_1907_01027_gb300.lmdg import Mesh, Quad
+    p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
+    arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
+    quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+    alpha = np.zeros(4 * 4 * len(p.w) * 2)
+    for (nx, ny), lay, a in (((0, 4), 1, None), ((4, 0), 1, None), ((4, 4), 2, alpha), ((4, 4), -1, alpha)):
+        mesh = Mesh(nx, ny, p.x0, p.y0, p.h)
+        h = ctypes.c_void_p()
+        rc = L.lmdg_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), arrs[3].ctypes.data,
+                          arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None if a is None else a.ctypes.data, lay,
+                          1.0, 0, None)
+        assert rc == -1, (nx, ny, lay)

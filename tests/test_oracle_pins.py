@@ -10,6 +10,8 @@
 * Reduced-system dimensions of Table tab-compare and unknown counts of Table tab-sndg-costper.
 * The RLMDG reduced system as printed does not reproduce the scheme; the corrected second row does.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -208,3 +210,25 @@ def test_rlm_printed_system_is_not_the_scheme():
         K_print[:, j] = col.ravel()
     Xp = np.linalg.solve(K_print, b_print).reshape(p.nx, 4)
     assert np.abs(Xp[:, 0] - good["X"][:, 0]).max() > 1e-6 * np.abs(good["X"][:, 0]).max()
+
+
+@pytest.mark.parametrize("variant", ["std", "lm", "rlm"])
+def test_rectangular_mesh_transpose_symmetry_and_dense(variant):
+    """Rectangular meshes (Section 2.1's mesh need not be square): the sweep oracle equals the dense one on a 3 x 5
+    and a 1 x 4 mesh, and swapping the axes maps the 3 x 5 problem onto the 5 x 3 one (the level-symmetric set is
+    invariant under Omega_x <-> Omega_y): cell (i, j) <-> (j, i), moments xi <-> eta, west/east <-> south/north
+    inflow data.  A mix-up of the row and column counts anywhere breaks one of these."""
+    from tests.helpers import random_problem
+    for n, m in ((3, 5), (1, 4)):
+        p = random_problem(n, 4, 0.6, 11, q_per_angle=False, ny=m)
+        p.alpha = np.random.default_rng(12).uniform(0, 1, (1, 4, max(n, m), 2)).repeat(p.nang, axis=0)
+        a = SweepOracle(p).solve(variant, direct=True)["phi"]
+        assert np.abs(a - dense.solve(p, variant)["phi"]).max() <= 1e-13 * np.abs(a).max()
+        t = copy.deepcopy(p)
+        t.n, t.ny = m, n
+        perm = np.arange(n * m).reshape(m, n).T.ravel()       # cell (j, i) of the transposed mesh
+        t.sigma_s, t.sigma_a = p.sigma_s[perm], p.sigma_a[perm]
+        t.q = p.q[perm][:, [0, 2, 1, 3]]
+        t.alpha = p.alpha[:, [2, 3, 0, 1]]
+        b = SweepOracle(t).solve(variant, direct=True)["phi"]
+        assert np.abs(b[:, [0, 2, 1, 3]] - a[perm]).max() <= 1e-12 * np.abs(a).max()

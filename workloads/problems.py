@@ -19,7 +19,7 @@ _D = np.array([1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0])   # int b_r^2 over the ref
 
 @dataclass
 class Problem:
-    n: int
+    n: int                       # cells along x
     h: float
     x0: float
     y0: float
@@ -30,13 +30,25 @@ class Problem:
     sigma_a: np.ndarray          # [n_x]
     q: np.ndarray                # [n_x][4] (layout 1) or [n_Omega][n_x][4] (layout 2)
     eps: float = 1.0
-    alpha: Optional[np.ndarray] = None   # [n_Omega][4][n][2] or None for vacuum
+    alpha: Optional[np.ndarray] = None   # [n_Omega][4][max(n, rows)][2] or None for vacuum (see face_count)
     name: str = ""
     info: dict = field(default_factory=dict)
+    ny: int = 0                  # cells along y (0: n, a square mesh)
+
+    @property
+    def rows(self):
+        """Cells along y."""
+        return self.ny or self.n
 
     @property
     def nx(self):
-        return self.n * self.n
+        """Number of cells."""
+        return self.n * self.rows
+
+    def face_count(self, side):
+        """Boundary faces of a side (0 west, 1 east: one per row; 2 south, 3 north: one per column).  ``alpha``
+        holds a side's faces in its first face_count(side) entries."""
+        return self.rows if side < 2 else self.n
 
     @property
     def nang(self):
@@ -48,7 +60,7 @@ class Problem:
 
     def cell_centres(self):
         c = self.x0 + (np.arange(self.n) + 0.5) * self.h
-        d = self.y0 + (np.arange(self.n) + 0.5) * self.h
+        d = self.y0 + (np.arange(self.rows) + 0.5) * self.h
         X, Y = np.meshgrid(c, d)          # [j][i]
         return X.ravel(), Y.ravel()
 
@@ -95,14 +107,15 @@ def legendre_project_face(f, n, h, x0, y0, npts=5):
     return out
 
 
-def uniform_problem(n, N, sigma_s, sigma_a, q, eps=1.0, L=1.0, x0=0.0, y0=0.0, name=""):
+def uniform_problem(n, N, sigma_s, sigma_a, q, eps=1.0, L=1.0, x0=0.0, y0=0.0, name="", ny=0):
+    """n x ny cells (ny = 0: n x n) of side L / n, constant media and source, S_N level-symmetric, vacuum."""
     ox, oy, w = level_symmetric_2d(N)
-    nx = n * n
+    nx = n * (ny or n)
     qq = np.zeros((nx, 4))
     qq[:, 0] = q
     return Problem(n=n, h=L / n, x0=x0, y0=y0, ox=ox, oy=oy, w=w,
                    sigma_s=np.full(nx, float(sigma_s)), sigma_a=np.full(nx, float(sigma_a)),
-                   q=qq, eps=eps, alpha=None, name=name)
+                   q=qq, eps=eps, alpha=None, name=name, ny=ny)
 
 
 def config1():
