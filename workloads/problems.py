@@ -153,7 +153,7 @@ def config4(eps=1.0, seed=1907, n=1024, N=16, patch=16):
     sigma_a patches), q = 1, vacuum inflow; eps in {1, 1e-3}."""
     p = uniform_problem(n, N, 1.0, 1.0, 1.0, eps=eps, name=f"{n}x{n}-S{N}-patch{patch}-eps{eps:g}")
     rng = np.random.default_rng(seed)
-    npch = n // patch
+    npch = -(-n // patch)                  # patches per side (the last one partial when patch does not divide n)
     ss = rng.uniform(0.1, 10.0, npch * npch).reshape(npch, npch)
     sa = rng.uniform(0.1, 10.0, npch * npch).reshape(npch, npch)
     jj, ii = np.meshgrid(np.arange(n) // patch, np.arange(n) // patch, indexing="ij")
