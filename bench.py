@@ -33,11 +33,19 @@ VARIANTS = ("std", "lm", "rlm")
 # reciprocals count 1): standard Q1 block solve, low-memory row-0 solve + L-row reductions, reconstructed.
 FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 
-# DRAM bytes (read + write) per launch of the FP32 non-storing sweep kernel, from one ncu capture of the
-# 512x512 S16 profiling case (bench.py --profile); the launch shape, hence the partial reductions per cell, is
-# the same at 1024x1024, so a full launch moves 4x these.  Must be re-measured whenever the kernel changes.
-SWEEP_DRAM_BYTES_512 = {"std": 23.055616e6 + 45.447680e6, "lm": 22.998784e6 + 12.470528e6,
-                        "rlm": 23.408896e6 + 85.924352e6}
+# One ncu capture of the FP32 non-storing sweep kernels (the lean instances GMRES runs) on the 512x512 S16
+# profiling case (bench.py --profile), per scheme: DRAM bytes read + written per launch (the launch shape, hence the
+# partial reductions per cell, is the same at 1024x1024, so a full launch moves 4x these), issue-active % of the
+# schedulers, warps active % of the maximum, and warp instructions per cell-direction update.  None until measured
+# for the current kernels; must be re-measured whenever the kernel changes.
+SWEEP_NCU_512 = {"std": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
+                         "inst_per_update": None},
+                 "lm": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
+                        "inst_per_update": None},
+                 "rlm": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
+                         "inst_per_update": None}}
+# the pipeline of the sweep: a strip of 32 rows takes n + 31 steps and the strip above starts 32 + 8 steps later
+STRIP_LAG = 40
 
 
 def workload_config():
@@ -275,7 +283,20 @@ def run_gpu(args, rank, ws, dist):
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = flops / (f32_ms / 1e3) / 1e12 if f32_ms > 0 else None
     scale = (p.n / 512) ** 2
-    traffic = sum(SWEEP_DRAM_BYTES_512[v] * scale * st["sweeps_fp32"] for v, st in stats) / max(1, f32_n)
+    measured = all(SWEEP_NCU_512[v]["dram_bytes"] is not None for v in VARIANTS)
+    traffic = (sum(SWEEP_NCU_512[v]["dram_bytes"] * scale * st["sweeps_fp32"] for v, st in stats) / max(1, f32_n)
+               if measured else None)
+    # the binding resource of the non-storing sweeps: instruction issue along the wavefront.  Critical path: the
+    # dependent steps of the last strip, (n + 31) + STRIP_LAG (strips - 1); its time per step from the launch time
+    strips = (p.n + 31) // 32
+    cp_steps = (p.n + 31) + STRIP_LAG * (strips - 1)
+    issue = {"critical_path_steps": cp_steps,
+             "ns_per_step": (f32_ms / max(1, f32_n)) * 1e6 / cp_steps if f32_n else None,
+             "issue_active_pct": {v: SWEEP_NCU_512[v]["issue_active_pct"] for v in VARIANTS},
+             "warps_active_pct": {v: SWEEP_NCU_512[v]["warps_active_pct"] for v in VARIANTS},
+             "warp_inst_per_update": {v: SWEEP_NCU_512[v]["inst_per_update"] for v in VARIANTS},
+             "source": "issue and warp figures from one ncu capture of the 512x512 profiling case (bench.py "
+                       "--profile), the kernels' launch shape being the same at 1024x1024"}
     roofline = {"bound": "alu", "kernel": "sweep_kernel<float> (all three schemes, non-storing)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
@@ -283,7 +304,7 @@ def run_gpu(args, rank, ws, dist):
                                   "case, per scheme, scaled by the cell count and averaged over the timed "
                                   "launches",
                 "peak_source": "FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 lanes x 2 x 2.07 GHz",
-                "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n,
+                "avg_launch_ms": f32_ms / max(1, f32_n), "launches": f32_n, "binding": issue,
                 "flops_per_update": FLOPS_PER_UPDATE,
                 "f32x2_sweep_avg_ms": f2_ms / max(1, f2_n), "f32x2_sweeps": f2_n,
                 "fp64_sweep_avg_ms": f64_ms / max(1, f64_n) if f64_n else None, "fp64_sweeps": f64_n}

@@ -152,8 +152,8 @@ def _same_material(p):
     return sx, sy
 
 
-def reconstruct(p, u0, alpha, suppress=False, three_cell=False):
-    """Upwind reconstruction R_alpha Pi_0 (Section 3.3.1), 2D P1 slopes only.
+def reconstruct(p, u0, alpha, suppress=False, three_cell=False, q1=False):
+    """Upwind reconstruction R_alpha Pi_0 (Section 3.3.1): 2D P1 slopes, and with ``q1`` the Q1-type term.
 
     ``u0``: cell averages ``[n_Omega][n_x]``.  Returns the Legendre coefficients ``[n_Omega][n_x][4]`` of
     (delta_x u)(x - x_i) + (delta_y u)(y - y_j): coefficient of b1 = xi is (h/2) delta_x, of b2 = eta is
@@ -164,7 +164,11 @@ def reconstruct(p, u0, alpha, suppress=False, three_cell=False):
     difference across such a face is zero.  ``three_cell`` (RLMDG*, Section 4.1): from the third cell on,
     delta is the slope at the cell centre of the quadratic with the cell averages of the cell and its two upwind
     neighbours, (3 u_i - 4 u_{i-1} + u_{i-2}) / (2h); the second cell keeps the two-cell difference and the
-    inflow cell the boundary difference.
+    inflow cell the boundary difference.  ``q1`` (the Q1-type reconstruction Section 3.3.1 mentions without a
+    formula; reading of this oracle): also the coefficient (h/2)^2 delta_xy of b3 = xi eta, delta_xy the upwind
+    y-difference of the reconstructed x-slopes delta_x, (delta_x(j) - delta_x(j -+ 1)) / h, and on the y-inflow
+    boundary row (delta_x - d alpha/dx) / (h/2) with d alpha/dx = 2 a1 / h along that boundary face (alpha None:
+    0); exact for bilinear functions, which the two-cell P1 reconstruction is not.
     """
     n, m, h, na = p.n, p.rows, p.h, p.nang
     out = np.zeros((na, n * m, 4))
@@ -208,12 +212,23 @@ def reconstruct(p, u0, alpha, suppress=False, three_cell=False):
                 dy[:-1, :] *= same_y
         out[l, :, 1] = (h / 2) * dx.ravel()
         out[l, :, 2] = (h / 2) * dy.ravel()
+        if q1:
+            dxy = np.zeros((m, n))
+            if p.oy[l] > 0:
+                dxy[1:, :] = (dx[1:, :] - dx[:-1, :]) / h
+                gS = 2.0 * alpha[l, 2, :n, 1] / h if alpha is not None else np.zeros(n)
+                dxy[0, :] = (dx[0, :] - gS) / (h / 2)
+            else:
+                dxy[:-1, :] = (dx[1:, :] - dx[:-1, :]) / h
+                gN = 2.0 * alpha[l, 3, :n, 1] / h if alpha is not None else np.zeros(n)
+                dxy[-1, :] = (gN - dx[-1, :]) / (h / 2)
+            out[l, :, 3] = (h / 2) ** 2 * dxy.ravel()
     return out
 
 
-def _Rstar(p, u0, alpha, suppress=False, three_cell=False):
+def _Rstar(p, u0, alpha, suppress=False, three_cell=False, q1=False):
     """R*_alpha applied to the piecewise constants u0: R_alpha Pi_0 u minus its angular average."""
-    R = reconstruct(p, u0, alpha, suppress, three_cell)
+    R = reconstruct(p, u0, alpha, suppress, three_cell, q1)
     return R - np.einsum("l,lkr->kr", p.w, R)[None]
 
 
@@ -243,7 +258,7 @@ def lm_basis(p):
     return E
 
 
-def rlm_trial_basis(p, suppress=False, three_cell=False):
+def rlm_trial_basis(p, suppress=False, three_cell=False, q1=False):
     """Trial basis of V_h^rlm: xi^{l,p,0} + R*_0 xi^{l,p,0}, then eta^{p,r} (Section 3.3.2)."""
     na, nx = p.nang, p.nx
     E = lm_basis(p)
@@ -252,12 +267,12 @@ def rlm_trial_basis(p, suppress=False, three_cell=False):
         for K in range(nx):
             u0 = np.zeros((na, nx))
             u0[l, K] = 1.0
-            Rs = _Rstar(p, u0, None, suppress, three_cell)
+            Rs = _Rstar(p, u0, None, suppress, three_cell, q1)
             Et[:, l * nx + K] += Rs.ravel()
     return Et
 
 
-def solve(p, variant, suppress=False, three_cell=False):
+def solve(p, variant, suppress=False, three_cell=False, q1=False):
     """Solve the discrete problem (``suppress``: RLMDG without reconstruction across cross-section jumps;
     ``three_cell``: RLMDG* with the three-cell reconstruction).
     Returns a dict with
@@ -286,8 +301,8 @@ def solve(p, variant, suppress=False, three_cell=False):
         out["phi1"] = c[na * nx:].reshape(nx, 3)
     elif variant == "rlm":
         E = lm_basis(p)
-        Et = rlm_trial_basis(p, suppress, three_cell)
-        rho = _Rstar(p, np.zeros((na, nx)), p.alpha, suppress, three_cell).ravel()   # affine part R*_alpha 0
+        Et = rlm_trial_basis(p, suppress, three_cell, q1)
+        rho = _Rstar(p, np.zeros((na, nx)), p.alpha, suppress, three_cell, q1).ravel()   # affine part R*_alpha 0
         c = np.linalg.solve(E.T @ B @ Et, E.T @ (Q - B @ rho))
         psi = (Et @ c + rho).reshape(na, nx, 4)
         out["psi0"] = c[:na * nx].reshape(na, nx)

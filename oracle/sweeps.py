@@ -67,12 +67,14 @@ class SweepOracle:
     """Matrix-free block operators of one problem.  ``threads`` angles are processed concurrently; every
     angular sum is accumulated in angle order, so results do not depend on the thread count."""
 
-    def __init__(self, p, threads=None, literal_b11=False, suppress=False, three_cell=False):
+    def __init__(self, p, threads=None, literal_b11=False, suppress=False, three_cell=False, q1=False):
         """``suppress``: RLMDG without reconstruction across cross-section jumps; ``three_cell``: RLMDG* (the
-        three-cell upwind reconstruction from the third cell on)."""
+        three-cell upwind reconstruction from the third cell on); ``q1``: the Q1-type reconstruction (also the
+        xi eta coefficient, see ``R``)."""
         self.p = p
         self.literal_b11 = literal_b11
         self.three_cell = three_cell
+        self.q1 = q1
         self.n, self.m, self.h, self.nx, self.na = p.n, p.rows, p.h, p.nx, p.nang
         self.suppress = suppress
         self.supp = self._suppression_bits() if suppress else None
@@ -285,8 +287,10 @@ class SweepOracle:
 
     # ---------------------------------------------------------------- RLMDG (Section 3.3)
     def R(self, l, u0, alpha=None):
-        """R_alpha Pi_0 for angle l: Legendre slope coefficients [n_x][2] ((h/2) delta_x, (h/2) delta_y);
-        with alpha None this is the linear part R, otherwise R u0 + r_alpha."""
+        """R_alpha Pi_0 for angle l: Legendre coefficients [n_x][3] of b1, b2, b3: ((h/2) delta_x, (h/2) delta_y,
+        (h/2)^2 delta_xy); with alpha None this is the linear part R, otherwise R u0 + r_alpha.  delta_xy is 0
+        except for the Q1-type reconstruction (``q1``): the upwind y-difference of the reconstructed x-slopes,
+        over h inside and h/2 against d alpha/dx = 2 a1 / h on the y-inflow boundary row."""
         n, m, h, p = self.n, self.m, self.h, self.p
         U = u0.reshape(m, n)
         bw = np.zeros(m) if alpha is None else alpha[l, 0, :m, 0]
@@ -321,18 +325,29 @@ class SweepOracle:
             bits = self.supp.reshape(m, n)
             dx = np.where(bits & (1 if p.ox[l] > 0 else 2), 0.0, dx)
             dy = np.where(bits & (4 if p.oy[l] > 0 else 8), 0.0, dy)
-        return np.stack([0.5 * h * dx.ravel(), 0.5 * h * dy.ravel()], axis=1)
+        dxy = np.zeros((m, n))
+        if self.q1:
+            if p.oy[l] > 0:
+                gS = np.zeros(n) if alpha is None else 2.0 * alpha[l, 2, :n, 1] / h
+                dxy = (dx - np.concatenate([gS[None, :], dx[:-1, :]], axis=0)) / \
+                    np.concatenate([np.full((1, n), h / 2), np.full((m - 1, n), h)], axis=0)
+            else:
+                gN = np.zeros(n) if alpha is None else 2.0 * alpha[l, 3, :n, 1] / h
+                dxy = (np.concatenate([dx[1:, :], gN[None, :]], axis=0) - dx) / \
+                    np.concatenate([np.full((m - 1, n), h), np.full((1, n), h / 2)], axis=0)
+        return np.stack([0.5 * h * dx.ravel(), 0.5 * h * dy.ravel(), 0.25 * h * h * dxy.ravel()], axis=1)
 
     def r_alpha(self, l):
-        return self.R(l, np.zeros(self.nx), self.p.alpha) if self.p.alpha is not None else np.zeros((self.nx, 2))
+        return self.R(l, np.zeros(self.nx), self.p.alpha) if self.p.alpha is not None else np.zeros((self.nx, 3))
 
     def P1(self, S):
         """P1 of a per-angle slope field S [n_Omega][n_x][k]: weighted angular sum."""
         return np.einsum("l,lkr->kr", self.p.w, S)
 
     def _slopes2(self, S2):
+        """Cell functions with the reconstructed coefficients S2 [n_x][3] of b1, b2, b3."""
         u = np.zeros((self.nx, 4))
-        u[:, 1:3] = S2
+        u[:, 1:] = S2
         return u
 
     def SigLt10(self, Psi0, P1R=None):
@@ -342,20 +357,18 @@ class SweepOracle:
 
         def one(l):
             u = self._const(Psi0[l])
-            u[:, 1:3] += self.R(l, Psi0[l]) - P1R
+            u[:, 1:] += self.R(l, Psi0[l]) - P1R
             return self.L(l, u)[:, 1:]
         return self._angles_sum(one, (self.nx, 3))
 
     def Gprime(self, Psi0):
         """Second block row operator: Sigma Ltilde10 + B11 P1 R."""
         P1R = self.P1(np.stack(self._angles_map(lambda l: self.R(l, Psi0[l]))))
-        P1R3 = np.zeros((self.nx, 3))
-        P1R3[:, :2] = P1R
-        return self.SigLt10(Psi0, P1R) + self.B11fast(P1R3)
+        return self.SigLt10(Psi0, P1R) + self.B11fast(P1R)
 
     def _rlm_Qt(self):
         """Qtilde0 (per angle) and Sigma Qtilde1, with Qtilde_r = Q_r - L_r1 (I - Sigma^T P1) r_alpha."""
-        ra = np.stack(self._angles_map(self.r_alpha))             # [n_Omega][n_x][2]
+        ra = np.stack(self._angles_map(self.r_alpha))             # [n_Omega][n_x][3]
         P1ra = self.P1(ra)
 
         def qt(l):
@@ -404,7 +417,7 @@ class SweepOracle:
         out = np.zeros((self.na, self.nx, 4))
         out[:, :, 0] = Psi0
         out[:, :, 1:] = Phi1[None]
-        out[:, :, 1:3] += RR
+        out[:, :, 1:] += RR
         return out
 
     # ---------------------------------------------------------------- P0-DG (V_{h,0}, Section 3.1)

@@ -425,6 +425,17 @@ void lmdg_destroy(lmdg_ctx *c) {
 int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *quad, const double *sigma_s,
                const double *sigma_a, const double *q, int q_layout, const double *alpha, int alpha_layout,
                double eps, int variant, const lmdg_options *opt) {
+  // LMDG_VERBOSE: the setup's phase times on stderr (each taken after a device synchronisation)
+  const bool verbose = std::getenv("LMDG_VERBOSE") != nullptr;
+  auto tphase = std::chrono::steady_clock::now();
+  auto phase = [&](const char *name) {
+    if (!verbose) return;
+    cudaDeviceSynchronize();
+    const auto t = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "lmdg_setup %-22s %8.3f ms\n", name,
+                 std::chrono::duration<double, std::milli>(t - tphase).count());
+    tphase = t;
+  };
   if (!out || !mesh || !quad || !sigma_s || !sigma_a || !q) return LMDG_ERR_ARG;
   *out = nullptr;
   const int ni = mesh->nx, nj = mesh->ny;
@@ -463,6 +474,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2) || o.precond < 0 || o.precond > 2 ||
       (o.precond == 2 && variant == LMDG_P0))
     return LMDG_ERR_ARG;
+  phase("validation");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return LMDG_ERR_CUDA;
   CK(cudaSetDevice(o.device));
@@ -583,6 +595,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     else rev[k] = found;
   }
   c->rev_ok = rev_ok;
+  phase("host tables");
   int e = 0;
   if (cudaMalloc(&c->perm, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMalloc(&c->rev, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
@@ -617,6 +630,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       }
     if ((e = upload(&c->supp, bits))) return fail(e);
   }
+  phase("uploads");
   c->g64 = choose_geom(c->kvar, nj, c->nq, 0);
   c->g32 = choose_geom(c->kvar, nj, c->nq, 1);
   c->g2 = choose_geom(c->kvar, nj, c->nq, 2);
@@ -639,6 +653,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   c->ctrl_words = 2 + (size_t)std::max({c->g64.units(), c->g32.units(), c->g2.units()});
   if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);
+  phase("work buffers");
   // FP64 element-solve coefficient tables per (material = distinct sigma_t h, direction class = distinct
   // (|Omega_x|, |Omega_y|)); the FP64 sweeps read them instead of forming the reciprocals and Schur products
   {
@@ -688,6 +703,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       c->coef = nullptr; c->mat = nullptr; c->cls = nullptr; c->matsh = nullptr;
     }
   }
+  phase("coefficient tables");
   if (o.precond == 2) {
     // vertex diffusion correction of the scheme's own diffusion limit (full gradient for Q1-DG, cell-averaged
     // gradient for the low-memory schemes), multigrid hierarchy built on the device
@@ -695,6 +711,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
                            0))
       return fail(e2);
   }
+  phase("diffusion correction");
   *out = c;
   return 0;
 }

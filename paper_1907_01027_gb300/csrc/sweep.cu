@@ -428,6 +428,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   const int gsize = (A.nq + A.g.groups - 1) / A.g.groups;
   const int g0 = grp * gsize;
   const int gcount = min(gsize, A.nq - g0);
+  // warps holding at least one direction (warp w holds directions w, w + W, ...); the others only stage data
+  // and take part in the barriers -- they skip the steps and the chunk sum leaves their slots out
+  const int Wact = min(W, gcount);
   const T c23 = (T)(2.0 / 3.0), c29 = (T)(2.0 / 9.0);
 
   // per-direction constants (signs of the quadrant folded in: the reduction is in the global frame)
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
     }
 
     // ---- C steps of the diagonal pipeline
-    if (!wabort) {
+    if (!wabort && warp < Wact) {
       for (int s = 0; s < C; ++s) {
         const int t = t0 + s;
         if (t >= nsteps) break;
@@ -842,7 +845,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       const size_t K = (size_t)jj * ni + ii;
       T sum[NR];
       load_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W) * 32 + l) * NR);   // warp 0, then the others in order
-      for (int ww = 1; ww < W; ++ww) {
+      for (int ww = 1; ww < Wact; ++ww) {
         add_nr<T, NR>(sum, red + ((size_t)((b * C + s) * W + ww) * 32 + l) * NR);
       }
       T *dst = A.part + ((size_t)pq * nx + K) * NR;
