@@ -107,7 +107,11 @@ typedef struct {
                           neighbours, (3 u_i - 4 u_{i-1} + u_{i-2}) / (2h) (the three-cell reconstruction of
                           Section 4.1); not combined with suppress; default 0 (two-cell, Section 3.3.1).  Its
                           sweep amplifies along rays through optically thin cells (sigma_t h below about 0.01 over
-                          hundreds of cells), where round-off then dominates */
+                          hundreds of cells), where round-off then dominates.  2: the Q1-type reconstruction
+                          (Section 3.3.1 names it without a formula): the two-cell slopes and the xi eta coefficient
+                          (h/2)^2 delta_xy, delta_xy the upwind y-difference of the reconstructed x-slopes (over h,
+                          and over h/2 against 2 a1 / h, the inflow data's derivative along the y-inflow face);
+                          exact for bilinear angular fluxes; not combined with suppress */
   int resid;           /* FP32 modes: arithmetic of the residual sweeps, LMDG_RESID_FP64 (default) or
                           LMDG_RESID_F32X2 */
 } lmdg_options;

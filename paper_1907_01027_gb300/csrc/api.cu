@@ -49,7 +49,10 @@ void free_pd(ProblemData<T> &p) {
   p = ProblemData<T>();
 }
 
-size_t part_elems(const SweepGeom &g, int nx) { return (size_t)4 * g.groups * nx * 6; }
+// partial reductions of a launch shape, in doubles (room for nr_of(kvar) values of any sweep arithmetic)
+size_t part_elems(const SweepGeom &g, int nx, int kvar) {
+  return (size_t)4 * g.groups * nx * (kvar == kRlmQ1 ? 8 : 6);
+}
 
 // Add the device time of the last recorded sweep launch to its precision's total (after a synchronisation,
 // or waiting for it when wait is set).
@@ -72,7 +75,7 @@ int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
   struct Item { const double *src; f2 **dst; size_t n; } items[] = {
       {c->d64.ox, &c->d2.ox, na}, {c->d64.oy, &c->d2.oy, na}, {c->d64.w, &c->d2.w, na},
       {c->d64.sigt, &c->d2.sigt, nx}, {c->d64.sse, &c->d2.sse, nx}, {c->d64.q, &c->d2.q, nq},
-      {c->d64.alpha, &c->d2.alpha, nal}, {c->p1ra64, &c->p1ra2, 2 * nx}, {c->coef, &c->coef2, ntab}};
+      {c->d64.alpha, &c->d2.alpha, nal}, {c->p1ra64, &c->p1ra2, 3 * nx}, {c->coef, &c->coef2, ntab}};
   // a failed allocation leaves the arrays made so far in place (freed by lmdg_destroy) for the next attempt
   for (auto &it : items) {
     if (it.n == 0 || it.src == nullptr) continue;
@@ -201,7 +204,7 @@ int check_error_word(lmdg_ctx *c, cudaStream_t s) {
 template <typename T, int VAR>
 __global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const double *__restrict__ X,
                            const double *__restrict__ p1ra, double *__restrict__ phi) {
-  constexpr int NR = VAR == kP0 ? 2 : ((VAR == 2) ? 6 : 4);
+  constexpr int NR = nr_of(VAR);
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   double s[NR];
@@ -213,10 +216,11 @@ __global__ void phi_kernel(int nx, int P, const T *__restrict__ part, const doub
   o[0] = s[0];
   if (VAR == kP0) { o[1] = 0; o[2] = 0; o[3] = 0; return; }
   o[1] = -x[1]; o[2] = -x[2]; o[3] = -x[3];
-  if (VAR == 2) {
-    o[1] += s[4] - (p1ra ? p1ra[2 * (size_t)K] : 0.0);
-    o[2] += s[5] - (p1ra ? p1ra[2 * (size_t)K + 1] : 0.0);
+  if (VAR == 2 || VAR == kRlmQ1) {
+    o[1] += s[4] - (p1ra ? p1ra[3 * (size_t)K] : 0.0);
+    o[2] += s[5] - (p1ra ? p1ra[3 * (size_t)K + 1] : 0.0);
   }
+  if (VAR == kRlmQ1) o[3] += s[6] - (p1ra ? p1ra[3 * (size_t)K + 2] : 0.0);
 }
 
 template <typename T>
@@ -225,6 +229,7 @@ cudaError_t launch_phi(lmdg_ctx *c, const T *part, int Pn, const double *X, doub
   add_launches(1);
   if (c->variant == LMDG_LM) phi_kernel<T, 1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
   else if (c->variant == LMDG_P0) phi_kernel<T, kP0><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, nullptr, P);
+  else if (c->kvar == kRlmQ1) phi_kernel<T, kRlmQ1><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
   else phi_kernel<T, 2><<<gs, bs, 0, s>>>(c->nx, Pn, part, X, c->p1ra64, P);
   return cudaGetLastError();
 }
@@ -469,7 +474,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   lmdg_default_options(&o);
   if (opt) o = *opt;
   if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
-      (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || (o.recon != 0 && o.recon != 1) ||
+      (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || o.recon < 0 || o.recon > 2 ||
       (o.recon && (variant != LMDG_RLM || o.suppress)) ||
       (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2) || o.precond < 0 || o.precond > 2 ||
       (o.precond == 2 && variant == LMDG_P0))
@@ -482,7 +487,9 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   lmdg_ctx *c = new (std::nothrow) lmdg_ctx();
   if (!c) return LMDG_ERR_NOMEM;
   c->ni = ni; c->nj = nj; c->nx = (int)nx; c->nang = na; c->nq = na / 4; c->variant = variant; c->q_layout = q_layout;
-  c->kvar = variant == LMDG_P0 ? kP0 : ((variant == LMDG_RLM && o.recon) ? kRlmStar : variant);
+  c->kvar = variant == LMDG_P0 ? kP0 : variant;
+  if (variant == LMDG_RLM && o.recon == 1) c->kvar = kRlmStar;
+  if (variant == LMDG_RLM && o.recon == 2) c->kvar = kRlmQ1;
   c->has_alpha = alpha != nullptr; c->dev = o.device; c->h = mesh->h; c->eps = eps;
   c->x0 = mesh->x0; c->y0 = mesh->y0; c->opt = o;
   auto fail = [&](int e) { lmdg_destroy(c); return e; };
@@ -529,7 +536,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
 
   // Sigma Q1 = sum_l w_l (eps int q_l b_r + inflow-boundary terms), r = 1..3 (low-memory right-hand sides)
   // P1 r_alpha = angular average of the boundary part of the reconstruction (RLMDG)
-  std::vector<double> sq1(nx * 3, 0.0), p1ra(nx * 2, 0.0);
+  std::vector<double> sq1(nx * 3, 0.0), p1ra(nx * 3, 0.0);
   const double h = mesh->h;
   const double D[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
   for (size_t K = 0; K < nx; ++K)
@@ -540,6 +547,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
         for (int l = 0; l < na; ++l) qs += quad->w[l] * q[((size_t)l * nx + K) * 4 + 1 + r];
       sq1[3 * K + r] = eps * h * h * D[r] * qs;
     }
+  const bool kvar_q1 = c->kvar == kRlmQ1;
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};
   for (int l = 0; l < na; ++l) {
     const double a = quad->ox[l], b = quad->oy[l], wl = quad->w[l];
@@ -555,7 +563,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       sq1[3 * K + 0] += wl * (-sx * aa * h * a0);
       sq1[3 * K + 1] += wl * (aa * h / 3.0 * a1);
       sq1[3 * K + 2] += wl * (-sx * aa * h / 3.0 * a1);
-      p1ra[2 * K + 0] += wl * sx * (-a0);
+      p1ra[3 * K + 0] += wl * sx * (-a0);
     }
     const int j0 = b > 0 ? 0 : nj - 1, offy = 2 * nj + (b > 0 ? 0 : ni);   // south / north faces
     for (int i = 0; i < ni; ++i) {
@@ -564,7 +572,24 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       sq1[3 * K + 0] += wl * (bb * h / 3.0 * a1);
       sq1[3 * K + 1] += wl * (-sy * bb * h * a0);
       sq1[3 * K + 2] += wl * (-sy * bb * h / 3.0 * a1);
-      p1ra[2 * K + 1] += wl * sy * (-a0);
+      p1ra[3 * K + 1] += wl * sy * (-a0);
+    }
+    if (kvar_q1) {
+      // Q1-type reconstruction: the xi eta coefficient of r_alpha (zero cell averages), in the direction's local
+      // frame rec3 = rec1 - a1 on the y-inflow row (a1 the along-face coefficient there, times sx) and
+      // (rec1 - rec1 of the cell below) / 2 above it, with rec1 = -a0 of the x-inflow face on the x-inflow
+      // column and 0 elsewhere; the global coefficient is sx sy rec3
+      auto rec1_loc = [&](int jr) { return -al[((size_t)offx + jr) * 2]; };
+      for (int i = 0; i < ni; ++i) {
+        const size_t K = (size_t)j0 * ni + i;
+        const double a1 = sx * al[((size_t)offy + i) * 2 + 1];
+        p1ra[3 * K + 2] += wl * sx * sy * ((i == i0 ? rec1_loc(j0) : 0.0) - a1);
+      }
+      for (int r = 1; r < nj; ++r) {
+        const int jr = b > 0 ? r : nj - 1 - r, jb = b > 0 ? r - 1 : nj - r;
+        const size_t K = (size_t)jr * ni + i0;
+        p1ra[3 * K + 2] += wl * sx * sy * 0.5 * (rec1_loc(jr) - rec1_loc(jb));
+      }
     }
   }
   c->Ax[0] = Ax[0]; c->Ax[1] = Ax[1]; c->Ay[0] = Ay[0]; c->Ay[1] = Ay[1];
@@ -641,7 +666,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
                  c->g64.warps, c->g64.apw, c->g32.groups, c->g32.warps, c->g32.apw, c->g2.groups, c->g2.warps,
                  c->g2.apw);
   const size_t pe =
-      std::max({part_elems(c->g64, c->nx), part_elems(c->g32, c->nx), part_elems(c->g2, c->nx)});
+      std::max({part_elems(c->g64, c->nx, c->kvar), part_elems(c->g32, c->nx, c->kvar),
+                part_elems(c->g2, c->nx, c->kvar)});
   if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   const int strips = (nj + 31) / 32;
   const size_t ytr_elems = (size_t)na * strips * ni * kTraceStride;

@@ -37,6 +37,9 @@ SweepGeom choose_geom(int variant, int nj, int nq, int prec) {
     apw = row0 ? 2 : 1;
     wmax = (row0 || variant == LMDG_STD) ? 4 : 8;
   } else { apw = variant == LMDG_LM ? 2 : 1; wmax = variant == LMDG_LM ? 6 : 8; }
+  // the Q1-type reconstruction's eight reduced values per cell: at most 6 warps keep a CTA's shared memory within
+  // two CTAs per SM (FP32) and within the per-CTA limit (float-float)
+  if (variant == kRlmQ1 && prec != 0 && wmax > 6) wmax = 6;
   int G = (nq + apw * wmax - 1) / (apw * wmax);
   while (G > 1 && (G - 1) * ((nq + G - 1) / G) >= nq) --G;
   const int gsize = (nq + G - 1) / G;

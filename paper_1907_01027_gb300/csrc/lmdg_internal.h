@@ -39,6 +39,12 @@ constexpr unsigned kTraceEmpty = 0xFFF7FFF7u;   // 32-bit pattern of a strip tra
 constexpr int kTraceStride = 4;      // trace values stored per (direction, strip boundary, column)
 constexpr int kRlmStar = 3;          // kernel variant of RLMDG* (LMDG_RLM with the three-cell reconstruction)
 constexpr int kP0 = 4;               // kernel variant of P0-DG (LMDG_P0)
+constexpr int kRlmQ1 = 5;            // kernel variant of RLMDG with the Q1-type reconstruction (also the xi eta term)
+// reduced values per cell (partial reductions; even, for paired moves) and trace values passed downwind per face
+constexpr int nr_of(int var) { return var == kP0 ? 2 : (var == kRlmQ1 ? 8 : (var >= 2 ? 6 : 4)); }
+constexpr int ns_of(int var) {
+  return var == kP0 ? 1 : ((var == kRlmStar || var == kRlmQ1) ? 4 : (var == 2 ? 3 : 2));
+}
 
 // Arguments of one sweep launch (everything a kernel reads or writes).
 template <typename T>
@@ -49,7 +55,7 @@ struct SweepArgs {
   ProblemData<T> pd;
   int q_per_angle;
   const double *X;     // [nx][4] input vector (always double)
-  const T *p1ra;       // [nx][2] P1 r_alpha (RLMDG, source sweeps) or null
+  const T *p1ra;       // [nx][3] P1 r_alpha (RLMDG, source sweeps) or null
   int source;          // 1: add eps q and the inflow data alpha
   T *part;             // [4*groups][nx][NR] partial reductions, written once each
   void *psi;           // storing sweep output or null: [nang (user order, through perm)][ni (column i)][nj (row j)]
@@ -142,7 +148,8 @@ cudaError_t quad_moments(int nang, const double *ox, const double *oy, const dou
 // Context
 struct lmdg_ctx {
   int ni = 0, nj = 0, nx = 0, nang = 0, nq = 0, variant = 0, q_layout = 0, has_alpha = 0, dev = 0;
-  int kvar = 0;                            // kernel variant: the scheme, kRlmStar for RLMDG*, kP0 for P0-DG
+  int kvar = 0;                            // kernel variant: the scheme, kRlmStar for RLMDG*, kRlmQ1 for the
+                                           // Q1-type reconstruction, kP0 for P0-DG
   double h = 0, eps = 0, x0 = 0, y0 = 0;
   lmdg_options opt{};
   int *perm = nullptr;                     // device [nang]
@@ -151,7 +158,7 @@ struct lmdg_ctx {
   lmdg::ProblemData<float> d32;
   lmdg::ProblemData<lmdg::f2> d2;          // float-float copies (residual sweeps of the mixed-precision solve)
   bool f2_ready = false;                   // d2, p1ra2 and coef2 hold the converted data
-  double *p1ra64 = nullptr;                // [nx][2]
+  double *p1ra64 = nullptr;                // [nx][3]
   float *p1ra32 = nullptr;
   lmdg::f2 *p1ra2 = nullptr;
   double *sq1 = nullptr;                   // [nx][3] Sigma Q1

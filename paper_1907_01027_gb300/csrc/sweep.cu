@@ -284,8 +284,8 @@ __device__ __forceinline__ int mat_of(f2 v) { return __float_as_int(v.hi); }
 // [2][kChunk][32], upstream traces [W][APW][kChunk][NS], RLMDG suppression bits [2][kChunk][32].
 template <typename T>
 size_t sweep_smem_bytes(int variant, int warps, int apw) {
-  const int NR = variant == kP0 ? 2 : (variant >= LMDG_RLM ? 6 : 4);
-  const int NS = variant == kP0 ? 1 : (variant == kRlmStar ? 4 : (variant == LMDG_RLM ? 3 : 2));
+  const int NR = nr_of(variant);
+  const int NS = ns_of(variant);
   return sizeof(T) * ((size_t)2 * kChunk * warps * NR * 32 + (size_t)2 * kChunk * 32 * 5 +
                       (size_t)warps * apw * kChunk * NS) +
          sizeof(unsigned) * (size_t)2 * kChunk * 32;
@@ -320,11 +320,14 @@ __global__ void prep_kernel(int nx, T h, T eps, const double *__restrict__ X, co
     o[1] = 0; o[2] = 0; o[3] = 0;
   } else {
     T p1 = 0, p2 = 0;
-    if (VAR >= 2 && source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; }
+    T p3 = 0;
+    if (VAR >= 2 && source && p1ra) {
+      p1 = p1ra[3 * (size_t)K]; p2 = p1ra[3 * (size_t)K + 1]; p3 = p1ra[3 * (size_t)K + 2];
+    }
     o[0] = 2 * h * (s * (T)Xa.x + eps * q4[0]);
     o[1] = -((T)Xa.y + p1);
     o[2] = -((T)Xb.x + p2);
-    o[3] = -(T)Xb.y;
+    o[3] = -((T)Xb.y + p3);
   }
   T *d = src + 4 * (size_t)K;
   d[0] = o[0]; d[1] = o[1]; d[2] = o[2]; d[3] = o[3];
@@ -392,8 +395,9 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 template <typename T, int VAR, int APW, bool TAB, bool LEAN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr bool P0 = VAR == kP0;         // P0-DG: the LMDG row-0 solve without slopes
-  constexpr int NR = P0 ? 2 : ((VAR >= 2) ? 6 : 4);   // reduced values per cell
-  constexpr int NS = P0 ? 1 : (VAR == 3 ? 4 : (VAR == 2 ? 3 : 2));   // trace values passed downwind per face
+  constexpr bool Q1R = VAR == kRlmQ1;     // RLMDG with the Q1-type reconstruction (the xi eta term)
+  constexpr int NR = nr_of(VAR);          // reduced values per cell
+  constexpr int NS = ns_of(VAR);          // trace values passed downwind per face
   constexpr int NC = (VAR == 1 || P0) ? 1 : 9;   // table coefficients per (material, class)
   constexpr int C = kChunk;
   // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
@@ -437,7 +441,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   int ang[APW], uA[APW], cA[APW], kA[APW];
   T wA[APW], aA[APW], bA[APW], c2a[APW], c2b[APW], c23a[APW], c23b[APW];
   T Wx[APW], Wy[APW];                 // w sx (2a, ...) / w sy (2b, ...): face terms of u0 (LM, RLM); w sx, w sy (STD)
-  T Dx[APW], Dy[APW], nWxb[APW], nWya[APW], W3a[APW], W3b[APW], wx[APW], wy[APW];   // RLMDG; W3*: w sx sy (STD)
+  T Dx[APW], Dy[APW], nWxb[APW], nWya[APW], W3a[APW], W3b[APW], wx[APW], wy[APW], wxy[APW];   // RLMDG; W3*: w sx sy
+                                                                                           // (STD)
   int nA = 0;
   T Ga = 0, Gb = 0;                   // LMDG: sum over the warp's directions of w 2/3 a, w 2/3 b
 #pragma unroll
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
       Dx[k] = flip(w * (2 * a + c23 * b), mx); Dy[k] = flip(w * (2 * b + c23 * a), my);
       nWxb[k] = flip(w * c23 * b, mx ^ 0x80000000u); nWya[k] = flip(w * c23 * a, my ^ 0x80000000u);
       W3a[k] = flip(w * c23 * a, mxy); W3b[k] = flip(w * c23 * b, mxy);
-      wx[k] = flip(w, mx); wy[k] = flip(w, my);
+      wx[k] = flip(w, mx); wy[k] = flip(w, my); wxy[k] = flip(w, mxy);
     }
   }
   // LMDG slope-trace terms, per lane: -sx Gb V1 (r = 1), -sy Ga U1 (r = 2), sx sy (Ga U1 + Gb V1) (r = 3)
@@ -795,19 +800,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 //   r=1: 2a (U0 - u0) + (2a + 2/3 b) rec1 - 2/3 b V1   (2/3 sigma_t h rec1: epilogue)
                 //   r=2: 2b (V0 - u0) + (2b + 2/3 a) rec2 - 2/3 a U1
                 //   r=3: 2/3 a (U1 - rec2) + 2/3 b (V1 - rec1)
-                if (use_corr) {
-                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                if constexpr (Q1R) {
+                  // Q1-type: u3 = A3 + rec3 with the xi eta coefficient rec3 = (h/2)^2 delta_xy, the upwind
+                  // y-difference of the x-slopes: (rec1 - rec1 of the cell below) / 2 inside, rec1 - a1 on the
+                  // y-inflow row (a1 the along-face coefficient of the inflow data there, local orientation).  It
+                  // adds 2/3 b rec3, 2/3 a rec3 and 2/3 (a + b) rec3 to rows 1, 2, 3 (2/9 sigma_t h rec3: epilogue)
+                  // and rides on the traces' slopes (U1, V1); row 0 does not see it
+                  const T rec3 = ybnd ? rec1 - ya1 : (T)0.5 * (rec1 - yin[3]);
+                  if (use_corr) {
+                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                  } else {
+                    acc[0] = fma(wl, u0, acc[0]);
+                    acc[1] = fma(nWxb[k], V1 - rec3, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
+                    acc[2] = fma(nWya[k], U1 - rec3, fma(Dy[k], rec2, fma(Wy[k], V0 - u0, acc[2])));
+                    acc[3] = fma(W3b[k], V1 - rec1 + rec3, fma(W3a[k], U1 - rec2 + rec3, acc[3]));
+                  }
+                  acc[4] = fma(wx[k], rec1, acc[4]);
+                  acc[5] = fma(wy[k], rec2, acc[5]);
+                  acc[6] = fma(wxy[k], rec3, acc[6]);
+                  xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2 + rec3; xs[k][2] = u0;
+                  ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1 + rec3; ys[k][2] = u0; ys[k][3] = rec1;
                 } else {
-                  acc[0] = fma(wl, u0, acc[0]);
-                  acc[1] = fma(nWxb[k], V1, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
-                  acc[2] = fma(nWya[k], U1, fma(Dy[k], rec2, fma(Wy[k], V0 - u0, acc[2])));
-                  acc[3] = fma(W3b[k], V1 - rec1, fma(W3a[k], U1 - rec2, acc[3]));
+                  if (use_corr) {
+                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                  } else {
+                    acc[0] = fma(wl, u0, acc[0]);
+                    acc[1] = fma(nWxb[k], V1, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
+                    acc[2] = fma(nWya[k], U1, fma(Dy[k], rec2, fma(Wy[k], V0 - u0, acc[2])));
+                    acc[3] = fma(W3b[k], V1 - rec1, fma(W3a[k], U1 - rec2, acc[3]));
+                  }
+                  acc[4] = fma(wx[k], rec1, acc[4]);
+                  acc[5] = fma(wy[k], rec2, acc[5]);
+                  if constexpr (VAR == 3) { xs[k][3] = Ux; ys[k][3] = Vy; }
+                  xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
+                  ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 }
-                acc[4] = fma(wx[k], rec1, acc[4]);
-                acc[5] = fma(wy[k], rec2, acc[5]);
-                if constexpr (VAR == 3) { xs[k][3] = Ux; ys[k][3] = Vy; }
-                xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
-                ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
@@ -888,7 +915,7 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
                                 const double *__restrict__ sigt, const double *__restrict__ qm,
                                 const double *__restrict__ p1ra, const double *__restrict__ sq1, int source,
                                 double *__restrict__ y) {
-  constexpr int NR = VAR == kP0 ? 2 : ((VAR >= 2) ? 6 : 4);
+  constexpr int NR = nr_of(VAR);
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nx) return;
   // the partials in index order, four quadrant-groups' loads in flight at a time.  FP32 partials are summed in
@@ -937,20 +964,25 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
     const double m = sse[K] * h * h;
     const double c = 2.0 / 3.0, sh = sigt[K] * h;
     const double Mw = qm[0], Ma = qm[1], Mb = qm[2], MOx = qm[3], MOy = qm[4];
-    double S1 = 0, S2 = 0, p1 = 0, p2 = 0;
+    double S1 = 0, S2 = 0, S3 = 0, p1 = 0, p2 = 0, p3 = 0;
     if constexpr (VAR >= 2) {
       S1 = s[4]; S2 = s[5];
-      if (source && p1ra) { p1 = p1ra[2 * (size_t)K]; p2 = p1ra[2 * (size_t)K + 1]; S1 -= p1; S2 -= p2; }
+      if constexpr (VAR == kRlmQ1) S3 = s[6];   // P1 R psi0 of the xi eta term (Q1-type reconstruction)
+      if (source && p1ra) {
+        p1 = p1ra[3 * (size_t)K]; p2 = p1ra[3 * (size_t)K + 1]; S1 -= p1; S2 -= p2;
+        if constexpr (VAR == kRlmQ1) { p3 = p1ra[3 * (size_t)K + 2]; S3 -= p3; }
+      }
     }
-    const double A1 = -(xa.y + p1), A2 = -(xb.x + p2), A3 = -xb.y;
+    const double A1 = -(xa.y + p1), A2 = -(xb.x + p2), A3 = -(xb.y + p3);
     double T1 = s[1] + (2 * Ma + c * Mb + c * sh * Mw) * A1 + c * MOy * A3;
     double T2 = s[2] + (2 * Mb + c * Ma + c * sh * Mw) * A2 + c * MOx * A3;
-    const double T3 = s[3] - c * MOy * A1 - c * MOx * A2 + (c * (Ma + Mb) + (2.0 / 9.0) * sh * Mw) * A3;
+    double T3 = s[3] - c * MOy * A1 - c * MOx * A2 + (c * (Ma + Mb) + (2.0 / 9.0) * sh * Mw) * A3;
     if constexpr (VAR >= 2) { T1 += c * sh * s[4]; T2 += c * sh * s[5]; }
+    if constexpr (VAR == kRlmQ1) T3 += (2.0 / 9.0) * sh * s[6];
     o0 = xa.x - s[0];
     o1 = m * (1.0 / 3.0) * (S1 - xa.y) - 0.5 * h * T1;
     o2 = m * (1.0 / 3.0) * (S2 - xb.x) - 0.5 * h * T2;
-    o3 = m * (1.0 / 9.0) * (0.0 - xb.y) - 0.5 * h * T3;
+    o3 = m * (1.0 / 9.0) * (S3 - xb.y) - 0.5 * h * T3;
     if (source && sq1) { o1 += sq1[3 * (size_t)K]; o2 += sq1[3 * (size_t)K + 1]; o3 += sq1[3 * (size_t)K + 2]; }
   }
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K) = make_double2(o0, o1);
@@ -984,6 +1016,7 @@ static const void *kernel_for_variant(int variant, int apw) {
     case LMDG_LM: return kernel_for<T, 1, TAB, LEAN>(apw);
     case LMDG_RLM: return kernel_for<T, 2, TAB, LEAN>(apw);
     case kRlmStar: return kernel_for<T, 3, TAB, LEAN>(apw);
+    case kRlmQ1: return kernel_for<T, kRlmQ1, TAB, LEAN>(apw);
     default: return kernel_for<T, kP0, TAB, LEAN>(apw);
   }
 }
@@ -1083,6 +1116,9 @@ cudaError_t launch_epilogue(int variant, int nx, int P, double h, const T *part,
       break;
     case kP0:
       epilogue_kernel<T, kP0><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
+      break;
+    case kRlmQ1:
+      epilogue_kernel<T, kRlmQ1><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);
       break;
     default:
       epilogue_kernel<T, 2><<<gs, bs, 0, s>>>(nx, P, h, part, X, sse, sigt, qm, p1ra, sq1, source, y);

@@ -86,13 +86,15 @@ def test_suppress_option_validated(L):
 
 
 def test_recon_option_validated(L):
-    """The three-cell reconstruction (RLMDG*) is RLMDG's only, takes 0 or 1 and excludes suppression."""
+    """The reconstructions (1: three-cell RLMDG*, 2: Q1-type) are RLMDG's only, take 0, 1 or 2 and exclude
+    suppression."""
     from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
     mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
     quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
-    for variant, recon, supp in ((0, 1, 0), (1, 1, 0), (3, 1, 0), (2, 2, 0), (2, 1, 1)):
+    for variant, recon, supp in ((0, 1, 0), (1, 1, 0), (3, 1, 0), (2, 3, 0), (2, -1, 0), (2, 1, 1), (2, 2, 1),
+                                 (0, 2, 0), (1, 2, 0)):
         o = Options()
         L.lmdg_default_options(ctypes.byref(o))
         o.recon = recon
