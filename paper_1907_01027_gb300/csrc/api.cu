@@ -262,6 +262,72 @@ int norm2(lmdg_ctx *c, const double *v, double *out_h, cudaStream_t s) {
   return 0;
 }
 
+// Per-cell tables of a problem, one thread per cell: sigma_t = sigma_s/eps + eps sigma_a and sigma_s/eps (FP64
+// and FP32); the source moments (q_layout 0: qin [N] expanded to q64 [N][4]; FP32 copy for layouts 0 and 1, layout
+// 2's is converted separately); the source part of Sigma Q1, eps h^2 D_r sum_l w_l q_l,r (layout 2: over the
+// sorted directions); P1 r_alpha = 0 (the inflow terms are added per boundary face afterwards); and the reciprocal
+// diagonal of B11, eps sigma_a h^2 D_r + (sum w |Omega_x|) h fx_r + (sum w |Omega_y|) h fy_r (the Jacobi scaling).
+__global__ void cell_tables_kernel(size_t nx, double eps, double h, const double *__restrict__ ss,
+                                   const double *__restrict__ sa, const double *qin, int q_layout, int nang,
+                                   const double *__restrict__ w, double Axs, double Ays, double *__restrict__ sigt64,
+                                   double *__restrict__ sse64, float *__restrict__ sigt32, float *__restrict__ sse32,
+                                   double *q64, float *__restrict__ q32, double *__restrict__ sq1,
+                                   double *__restrict__ p1ra, double *__restrict__ bdinv) {
+  const size_t K = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double D[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
+  const double fx[3] = {1.0, 1.0 / 3.0, 1.0 / 3.0}, fy[3] = {1.0 / 3.0, 1.0, 1.0 / 3.0};
+  const double se = ss[K] / eps, st = se + eps * sa[K];
+  sigt64[K] = st; sse64[K] = se; sigt32[K] = (float)st; sse32[K] = (float)se;
+  double qs[3] = {0, 0, 0};
+  if (q_layout == 0) {
+    const double q0 = qin[K];
+    q64[4 * K] = q0; q64[4 * K + 1] = 0; q64[4 * K + 2] = 0; q64[4 * K + 3] = 0;
+    q32[4 * K] = (float)q0; q32[4 * K + 1] = 0; q32[4 * K + 2] = 0; q32[4 * K + 3] = 0;
+  } else if (q_layout == 1) {
+    for (int r = 0; r < 4; ++r) q32[4 * K + r] = (float)q64[4 * K + r];
+    for (int r = 0; r < 3; ++r) qs[r] = q64[4 * K + 1 + r];
+  } else {
+    for (int l = 0; l < nang; ++l)
+      for (int r = 0; r < 3; ++r) qs[r] += w[l] * q64[((size_t)l * nx + K) * 4 + 1 + r];
+  }
+  for (int r = 0; r < 3; ++r) {
+    sq1[3 * K + r] = eps * h * h * D[r] * qs[r];
+    p1ra[3 * K + r] = 0.0;
+    bdinv[3 * K + r] = 1.0 / (eps * sa[K] * h * h * D[r] + Axs * h * fx[r] + Ays * h * fy[r]);
+  }
+}
+
+// Adds the inflow terms summed per boundary face (bnd[face][6]: Sigma Q1 r = 1..3, P1 r_alpha r = 1..3; faces
+// west, east by row, south, north by column) to the face's cell, for one side
+__global__ void boundary_terms_kernel(int ni, int nj, int side, const double *__restrict__ bnd,
+                                      double *__restrict__ sq1, double *__restrict__ p1ra) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int count = side < 2 ? nj : ni;
+  if (f >= count) return;
+  const int off = side == 0 ? 0 : (side == 1 ? nj : (side == 2 ? 2 * nj : 2 * nj + ni));
+  const size_t K = side == 0 ? (size_t)f * ni : (side == 1 ? (size_t)f * ni + ni - 1
+                                                            : (side == 2 ? (size_t)f : (size_t)(nj - 1) * ni + f));
+  const double *b = bnd + (size_t)(off + f) * 6;
+  for (int r = 0; r < 3; ++r) {
+    sq1[3 * K + r] += b[r];
+    p1ra[3 * K + r] += b[3 + r];
+  }
+}
+
+__global__ void to_float_kernel(size_t n, const double *__restrict__ x, float *__restrict__ y) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    y[k] = (float)x[k];
+}
+
+cudaError_t to_float(const double *x, float *y, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  add_launches(1);
+  const size_t g = std::min<size_t>((n + 255) / 256, 4096);
+  to_float_kernel<<<(unsigned)g, 256, 0, s>>>(n, x, y);
+  return cudaGetLastError();
+}
+
 // y = Minv x: the right preconditioner of GMRES -- diag(I, diag(B11))^-1 for the low-memory schemes (precond >= 1),
 // then with precond = 2 the vertex diffusion correction y += I_h D_a^-1 R_h (sigma_s/eps) y (one V-cycle)
 int apply_minv(lmdg_ctx *c, double *y, const double *x, cudaStream_t s) {
@@ -504,21 +570,16 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   std::copy(perm.begin(), perm.end(), c->perm_h);
   std::vector<double> ox(na), oy(na), w(na);
   for (int k = 0; k < na; ++k) { ox[k] = quad->ox[perm[k]]; oy[k] = quad->oy[perm[k]]; w[k] = quad->w[perm[k]]; }
-  std::vector<double> sigt(nx), sse(nx);
-  for (size_t K = 0; K < nx; ++K) { sigt[K] = sigma_s[K] / eps + eps * sigma_a[K]; sse[K] = sigma_s[K] / eps; }
+  // angle-dependent sources are reordered to the sorted directions on the host; constant and per-cell sources go
+  // up as given and the device forms the rest of the per-cell tables (cell_tables_kernel)
   std::vector<double> qv;
-  if (q_layout == 0) {
-    qv.assign(nx * 4, 0.0);
-    for (size_t K = 0; K < nx; ++K) qv[4 * K] = q[K];
-  } else if (q_layout == 1) {
-    // the caller's array is uploaded as it is (qsrc below)
-  } else {
+  if (q_layout == 2) {
     qv.resize((size_t)na * nx * 4);
     for (int k = 0; k < na; ++k)
       std::memcpy(&qv[(size_t)k * nx * 4], q + (size_t)perm[k] * nx * 4, sizeof(double) * nx * 4);
   }
-  const double *qsrc = q_layout == 1 ? q : qv.data();
-  const size_t qn = q_layout == 1 ? nx * 4 : qv.size();
+  const double *qsrc = q_layout == 2 ? qv.data() : q;
+  const size_t qn = q_layout == 0 ? nx : (q_layout == 1 ? nx * 4 : qv.size());
   // inflow data per direction: [2 nj + 2 ni][2] (west and east faces by row, south and north faces by column);
   // alpha_layout 0 expands the single value given to every face and direction (a0 = value, a1 = 0)
   const size_t per = (size_t)2 * (ni + nj) * 2;
@@ -534,19 +595,14 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     for (int k = 0; k < na; ++k) std::memcpy(&av[(size_t)k * per], alpha + (size_t)perm[k] * per, sizeof(double) * per);
   }
 
-  // Sigma Q1 = sum_l w_l (eps int q_l b_r + inflow-boundary terms), r = 1..3 (low-memory right-hand sides)
-  // P1 r_alpha = angular average of the boundary part of the reconstruction (RLMDG)
-  std::vector<double> sq1(nx * 3, 0.0), p1ra(nx * 3, 0.0);
+  // Sigma Q1 = sum_l w_l (eps int q_l b_r + inflow-boundary terms), r = 1..3 (low-memory right-hand sides) and
+  // P1 r_alpha = angular average of the boundary part of the reconstruction (RLMDG): the device forms the source
+  // part of Sigma Q1; the inflow terms live on the boundary faces and are summed here per face, in the face order
+  // of the inflow data (west and east by row, south and north by column), [face][sigma Q1 r = 1..3, P1 r_alpha
+  // r = 1..3], and added to the face's cell on the device
   const double h = mesh->h;
-  const double D[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
-  for (size_t K = 0; K < nx; ++K)
-    for (int r = 0; r < 3; ++r) {
-      double qs = 0;
-      if (q_layout == 1) qs = q[4 * K + 1 + r];
-      else if (q_layout == 2)
-        for (int l = 0; l < na; ++l) qs += quad->w[l] * q[((size_t)l * nx + K) * 4 + 1 + r];
-      sq1[3 * K + r] = eps * h * h * D[r] * qs;
-    }
+  const int nfaces = 2 * (ni + nj);
+  std::vector<double> bnd(alpha ? (size_t)nfaces * 6 : 0, 0.0);
   const bool kvar_q1 = c->kvar == kRlmQ1;
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};
   for (int l = 0; l < na; ++l) {
@@ -558,37 +614,36 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     const double *al = alpha + (size_t)l * per;
     const int i0 = a > 0 ? 0 : ni - 1, offx = a > 0 ? 0 : nj;           // west / east faces
     for (int j = 0; j < nj; ++j) {
-      const size_t K = (size_t)j * ni + i0;
       const double a0 = al[((size_t)offx + j) * 2], a1 = al[((size_t)offx + j) * 2 + 1];
-      sq1[3 * K + 0] += wl * (-sx * aa * h * a0);
-      sq1[3 * K + 1] += wl * (aa * h / 3.0 * a1);
-      sq1[3 * K + 2] += wl * (-sx * aa * h / 3.0 * a1);
-      p1ra[3 * K + 0] += wl * sx * (-a0);
+      double *f = &bnd[((size_t)offx + j) * 6];
+      f[0] += wl * (-sx * aa * h * a0);
+      f[1] += wl * (aa * h / 3.0 * a1);
+      f[2] += wl * (-sx * aa * h / 3.0 * a1);
+      f[3] += wl * sx * (-a0);
     }
     const int j0 = b > 0 ? 0 : nj - 1, offy = 2 * nj + (b > 0 ? 0 : ni);   // south / north faces
     for (int i = 0; i < ni; ++i) {
-      const size_t K = (size_t)j0 * ni + i;
       const double a0 = al[((size_t)offy + i) * 2], a1 = al[((size_t)offy + i) * 2 + 1];
-      sq1[3 * K + 0] += wl * (bb * h / 3.0 * a1);
-      sq1[3 * K + 1] += wl * (-sy * bb * h * a0);
-      sq1[3 * K + 2] += wl * (-sy * bb * h / 3.0 * a1);
-      p1ra[3 * K + 1] += wl * sy * (-a0);
+      double *f = &bnd[((size_t)offy + i) * 6];
+      f[0] += wl * (bb * h / 3.0 * a1);
+      f[1] += wl * (-sy * bb * h * a0);
+      f[2] += wl * (-sy * bb * h / 3.0 * a1);
+      f[4] += wl * sy * (-a0);
     }
     if (kvar_q1) {
       // Q1-type reconstruction: the xi eta coefficient of r_alpha (zero cell averages), in the direction's local
       // frame rec3 = rec1 - a1 on the y-inflow row (a1 the along-face coefficient there, times sx) and
       // (rec1 - rec1 of the cell below) / 2 above it, with rec1 = -a0 of the x-inflow face on the x-inflow
-      // column and 0 elsewhere; the global coefficient is sx sy rec3
+      // column and 0 elsewhere; the global coefficient is sx sy rec3.  The corner cell's term goes with its
+      // y-inflow face, the rest of the x-inflow column's with their x-inflow faces
       auto rec1_loc = [&](int jr) { return -al[((size_t)offx + jr) * 2]; };
       for (int i = 0; i < ni; ++i) {
-        const size_t K = (size_t)j0 * ni + i;
         const double a1 = sx * al[((size_t)offy + i) * 2 + 1];
-        p1ra[3 * K + 2] += wl * sx * sy * ((i == i0 ? rec1_loc(j0) : 0.0) - a1);
+        bnd[((size_t)offy + i) * 6 + 5] += wl * sx * sy * ((i == i0 ? rec1_loc(j0) : 0.0) - a1);
       }
       for (int r = 1; r < nj; ++r) {
         const int jr = b > 0 ? r : nj - 1 - r, jb = b > 0 ? r - 1 : nj - r;
-        const size_t K = (size_t)jr * ni + i0;
-        p1ra[3 * K + 2] += wl * sx * sy * 0.5 * (rec1_loc(jr) - rec1_loc(jb));
+        bnd[((size_t)offx + jr) * 6 + 5] += wl * sx * sy * 0.5 * (rec1_loc(jr) - rec1_loc(jb));
       }
     }
   }
@@ -599,15 +654,6 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     qm[0] += w[l]; qm[1] += w[l] * std::fabs(ox[l]); qm[2] += w[l] * std::fabs(oy[l]);
     qm[3] += w[l] * ox[l]; qm[4] += w[l] * oy[l];
   }
-  // diagonal of B11: eps sigma_a h^2 D_r + outflow face terms (Jacobi right preconditioner)
-  std::vector<double> bdinv(nx * 3);
-  const double fx[3] = {1.0, 1.0 / 3.0, 1.0 / 3.0}, fy[3] = {1.0 / 3.0, 1.0, 1.0 / 3.0};
-  for (size_t K = 0; K < nx; ++K)
-    for (int r = 0; r < 3; ++r)
-      bdinv[3 * K + r] =   // the preconditioner multiplies by the reciprocal
-          1.0 / (eps * sigma_a[K] * h * h * D[r] + (Ax[0] + Ax[1]) * h * fx[r] + (Ay[0] + Ay[1]) * h * fy[r]);
-
-
   // opposite direction of every sorted direction (central symmetry, needed by the adjoint)
   std::vector<int> rev(na, 0);
   bool rev_ok = true;
@@ -628,13 +674,58 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     return fail(LMDG_ERR_CUDA);
   if (cudaMemcpy(c->perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LMDG_ERR_CUDA);
+  // the problem data goes up as given (cross sections, source) and the device forms the per-cell tables
+  double *ss_dev = nullptr, *q0_dev = nullptr;
+  const size_t nq4 = q_layout == 2 ? qn : nx * 4;
   if ((e = upload(&c->d64.ox, ox)) || (e = upload(&c->d64.oy, oy)) || (e = upload(&c->d64.w, w)) ||
-      (e = upload(&c->d64.sigt, sigt)) || (e = upload(&c->d64.sse, sse)) || (e = upload(&c->d64.q, qsrc, qn)) ||
       (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
-      (e = upload(&c->d32.sigt, sigt)) || (e = upload(&c->d32.sse, sse)) || (e = upload(&c->d32.q, qsrc, qn)) ||
-      (e = upload(&c->p1ra64, p1ra)) || (e = upload(&c->p1ra32, p1ra)) || (e = upload(&c->sq1, sq1)) ||
-      (e = upload(&c->b11dinv, bdinv)) || (e = upload(&c->sigma_a, sigma_a, nx)) || (e = upload(&c->qmom, qm)))
+      (e = upload(&ss_dev, sigma_s, nx)) || (e = upload(&c->sigma_a, sigma_a, nx)) || (e = upload(&c->qmom, qm)) ||
+      (q_layout == 0 && (e = upload(&q0_dev, qsrc, qn)))) {
+    cudaFree(ss_dev);
+    cudaFree(q0_dev);
     return fail(e);
+  }
+  if ((q_layout == 0 && cudaMalloc(&c->d64.q, sizeof(double) * nq4) != cudaSuccess) ||
+      (q_layout != 0 && (e = upload(&c->d64.q, qsrc, qn)))) {
+    cudaFree(ss_dev);
+    cudaFree(q0_dev);
+    return fail(e ? e : LMDG_ERR_NOMEM);
+  }
+  bool ok = cudaMalloc(&c->d64.sigt, sizeof(double) * nx) == cudaSuccess &&
+            cudaMalloc(&c->d64.sse, sizeof(double) * nx) == cudaSuccess &&
+            cudaMalloc(&c->d32.sigt, sizeof(float) * nx) == cudaSuccess &&
+            cudaMalloc(&c->d32.sse, sizeof(float) * nx) == cudaSuccess &&
+            cudaMalloc(&c->d32.q, sizeof(float) * nq4) == cudaSuccess &&
+            cudaMalloc(&c->sq1, sizeof(double) * 3 * nx) == cudaSuccess &&
+            cudaMalloc(&c->p1ra64, sizeof(double) * 3 * nx) == cudaSuccess &&
+            cudaMalloc(&c->p1ra32, sizeof(float) * 3 * nx) == cudaSuccess &&
+            cudaMalloc(&c->b11dinv, sizeof(double) * 3 * nx) == cudaSuccess;
+  if (ok) {
+    add_launches(1);
+    cell_tables_kernel<<<(unsigned)((nx + 255) / 256), 256>>>(
+        nx, eps, h, ss_dev, c->sigma_a, q_layout == 0 ? q0_dev : c->d64.q, q_layout, na, c->d64.w, Ax[0] + Ax[1],
+        Ay[0] + Ay[1], c->d64.sigt, c->d64.sse, c->d32.sigt, c->d32.sse, c->d64.q, c->d32.q, c->sq1, c->p1ra64,
+        c->b11dinv);
+    ok = cudaGetLastError() == cudaSuccess;
+  }
+  if (ok && q_layout == 2) ok = to_float(c->d64.q, c->d32.q, nq4, 0) == cudaSuccess;
+  if (ok && alpha) {
+    double *bnd_dev = nullptr;
+    if ((e = upload(&bnd_dev, bnd))) { cudaFree(ss_dev); cudaFree(q0_dev); return fail(e); }
+    for (int side = 0; side < 4 && ok; ++side) {   // one side per launch: a corner cell has faces on two sides
+      const int count = side < 2 ? nj : ni;
+      add_launches(1);
+      boundary_terms_kernel<<<(count + 255) / 256, 256>>>(ni, nj, side, bnd_dev, c->sq1, c->p1ra64);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+    cudaFree(bnd_dev);
+  }
+  if (ok) ok = to_float(c->p1ra64, c->p1ra32, 3 * nx, 0) == cudaSuccess;
+  ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+  cudaFree(ss_dev);
+  cudaFree(q0_dev);
+  if (!ok) return fail(LMDG_ERR_CUDA);
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
   }
@@ -684,7 +775,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   // (|Omega_x|, |Omega_y|)); the FP64 sweeps read them instead of forming the reciprocals and Schur products
   {
     std::vector<double> sh(nx);
-    for (size_t K = 0; K < nx; ++K) sh[K] = sigt[K] * h;
+    for (size_t K = 0; K < nx; ++K) sh[K] = (sigma_s[K] / eps + eps * sigma_a[K]) * h;
     // distinct values, sorted: runs of equal neighbours (piecewise-constant media) are skipped before the sort,
     // and a cell equal to its predecessor takes its index without a search
     std::vector<double> uniq;

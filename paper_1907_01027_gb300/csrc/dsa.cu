@@ -12,8 +12,9 @@
 //
 // Vertex (I, J), I along x, of the (ni + 1) x (nj + 1) vertices of ni x nj cells has index J (ni + 1) + I.
 // Operators are nine-point stencils of bs x bs blocks, A[v][k][r][c] with k = (dJ + 1) * 3 + (dI + 1) the
-// neighbour (I + dI, J + dJ).  Levels halve the cells along x and y while both numbers are even and above 2.  Prolongation is bilinear per component; for the cell-average
-// stiffness the first coarsening carries two components per coarse vertex, P = [P_bl, C P_bl] with
+// neighbour (I + dI, J + dJ).  Levels halve the cells along x and y while both numbers are even and above 2.
+// Prolongation is bilinear per component; for the cell-average stiffness the first coarsening carries two
+// components per coarse vertex, P = [P_bl, C P_bl] with
 // C = diag((-1)^(I+J)) (its gradient part leaves the two lattices I + J even / odd decoupled, so functions smooth
 // on each lattice are what the coarse space must hold).  Coarse operators are Galerkin products P^T A P computed
 // on the device, one coarse vertex per thread in a fixed order.  Smoothing: nu damped block-Jacobi steps before

@@ -1,4 +1,4 @@
-"""Pins of the Q1-type reconstruction (Section 3.3.1 names it, "similar results", and gives no formula).
+"""Pins of the Q1-type reconstruction (Section 3.3.1 mentions it as converging alike and gives no formula).
 
 Reading: besides the two-cell P1 slopes, the coefficient (h/2)^2 delta_xy of b3 = xi eta, delta_xy the upwind
 y-difference of the reconstructed x-slopes (spacing h, and h/2 against the derivative 2 a1 / h of the inflow data
