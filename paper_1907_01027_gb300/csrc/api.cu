@@ -49,10 +49,6 @@ void free_pd(ProblemData<T> &p) {
   p = ProblemData<T>();
 }
 
-// partial reductions of a launch shape, in doubles (room for nr_of(kvar) values of any sweep arithmetic)
-size_t part_elems(const SweepGeom &g, int nx, int kvar) {
-  return (size_t)4 * g.groups * nx * (kvar == kRlmQ1 ? 8 : 6);
-}
 
 // Add the device time of the last recorded sweep launch to its precision's total (after a synchronisation,
 // or waiting for it when wait is set).
@@ -107,6 +103,17 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.q_per_angle = c->q_layout == 2;
   a.X = X;
   a.source = source;
+  {
+    // partial reductions of this launch shape and arithmetic: the buffer grows to the largest one used
+    const size_t pbytes = (size_t)4 * a.g.groups * c->nx * nr_of(c->kvar) * sizeof(T);
+    if (c->part_bytes < pbytes) {
+      cudaFree(c->part);
+      c->part = nullptr;
+      c->part_bytes = 0;
+      if (cudaMalloc(&c->part, pbytes) != cudaSuccess) { c->part = nullptr; return LMDG_ERR_NOMEM; }
+      c->part_bytes = pbytes;
+    }
+  }
   a.part = reinterpret_cast<T *>(c->part);
   a.perm = c->perm;
   a.ytr = reinterpret_cast<T *>(c->ytr);
@@ -142,12 +149,15 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     int kind = f64 ? 0 : (bf16 && c->variant != LMDG_STD ? 2 : 1);
     size_t per = c->variant == LMDG_STD ? 4 : 1;
     size_t elems = (size_t)c->nang * c->nx * per;
-    size_t bytes = elems * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
-    if (c->psi == nullptr) {
-      // sized for the widest kind so any precision can reuse the buffer
-      if (cudaMalloc(&c->psi, elems * 8) != cudaSuccess) return LMDG_ERR_NOMEM;
+    const size_t bytes = elems * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
+    if (c->psi_bytes < bytes) {   // grown to the widest kind stored so far (cudaFree waits for earlier use)
+      cudaFree(c->psi);
+      c->psi = nullptr;
+      c->psi_bytes = 0;
+      c->psi_kind = -1;
+      if (cudaMalloc(&c->psi, bytes) != cudaSuccess) { c->psi = nullptr; return LMDG_ERR_NOMEM; }
+      c->psi_bytes = bytes;
     }
-    (void)bytes;
     c->psi_kind = kind;
     c->psi_elems = elems;
     a.psi = c->psi;
@@ -313,6 +323,25 @@ __global__ void boundary_terms_kernel(int ni, int nj, int side, const double *__
     sq1[3 * K + r] += b[r];
     p1ra[3 * K + r] += b[3 + r];
   }
+}
+
+// Material index of every cell: the entry of the sorted distinct values matsh[0..nmat) nearest to sigma_t h
+// (the host formed matsh from the same formula; nearest rather than equal absorbs a last-bit difference between
+// host and device arithmetic)
+__global__ void material_kernel(size_t nx, double h, const double *__restrict__ sigt, const double *__restrict__ matsh,
+                                int nmat, int *__restrict__ mat) {
+  const size_t K = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double v = sigt[K] * h;
+  int lo = 0, hi = nmat;                  // first entry >= v
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (matsh[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  int m = lo < nmat ? lo : nmat - 1;
+  if (lo > 0 && (lo == nmat || fabs(matsh[lo - 1] - v) <= fabs(matsh[lo] - v))) m = lo - 1;
+  mat[K] = m;
 }
 
 __global__ void to_float_kernel(size_t n, const double *__restrict__ x, float *__restrict__ y) {
@@ -756,10 +785,6 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
                  "groups=%d warps=%d apw=%d | f32x2 groups=%d warps=%d apw=%d\n", ni, nj, na, variant, c->g64.groups,
                  c->g64.warps, c->g64.apw, c->g32.groups, c->g32.warps, c->g32.apw, c->g2.groups, c->g2.warps,
                  c->g2.apw);
-  const size_t pe =
-      std::max({part_elems(c->g64, c->nx, c->kvar), part_elems(c->g32, c->nx, c->kvar),
-                part_elems(c->g2, c->nx, c->kvar)});
-  if (cudaMalloc(&c->part, sizeof(double) * pe) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   const int strips = (nj + 31) / 32;
   const size_t ytr_elems = (size_t)na * strips * ni * kTraceStride;
   if (cudaMalloc(&c->ytr, sizeof(double) * ytr_elems) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
@@ -774,20 +799,17 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   // FP64 element-solve coefficient tables per (material = distinct sigma_t h, direction class = distinct
   // (|Omega_x|, |Omega_y|)); the FP64 sweeps read them instead of forming the reciprocals and Schur products
   {
-    std::vector<double> sh(nx);
-    for (size_t K = 0; K < nx; ++K) sh[K] = (sigma_s[K] / eps + eps * sigma_a[K]) * h;
-    // distinct values, sorted: runs of equal neighbours (piecewise-constant media) are skipped before the sort,
-    // and a cell equal to its predecessor takes its index without a search
+    // distinct values of sigma_t h, sorted (runs of equal neighbours -- piecewise-constant media -- are skipped
+    // before the sort); each cell's material index is then found on the device (material_kernel)
     std::vector<double> uniq;
-    for (size_t K = 0; K < nx; ++K)
-      if (K == 0 || sh[K] != sh[K - 1]) uniq.push_back(sh[K]);
+    double prev = 0.0;
+    for (size_t K = 0; K < nx; ++K) {
+      const double shK = (sigma_s[K] / eps + eps * sigma_a[K]) * h;
+      if (K == 0 || shK != prev) uniq.push_back(shK);
+      prev = shK;
+    }
     std::sort(uniq.begin(), uniq.end());
     uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-    std::vector<int> matv(nx);
-    for (size_t K = 0; K < nx; ++K)
-      matv[K] = (K > 0 && sh[K] == sh[K - 1])
-                    ? matv[K - 1]
-                    : (int)(std::lower_bound(uniq.begin(), uniq.end(), sh[K]) - uniq.begin());
     std::vector<double> cab;
     std::vector<int> clsv(na);
     for (int k = 0; k < na; ++k) {
@@ -807,12 +829,15 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
               cudaMalloc(&c->cls, sizeof(int) * na) == cudaSuccess &&
               cudaMalloc(&c->matsh, sizeof(double) * c->nmat) == cudaSuccess &&
               cudaMalloc(&cabd, sizeof(double) * cab.size()) == cudaSuccess;
-    ok = ok && cudaMemcpy(c->mat, matv.data(), sizeof(int) * nx, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->cls, clsv.data(), sizeof(int) * na, cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = ok && cudaMemcpy(c->cls, clsv.data(), sizeof(int) * na, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(c->matsh, uniq.data(), sizeof(double) * c->nmat, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(cabd, cab.data(), sizeof(double) * cab.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         build_coef_tables(c->kvar, c->nmat, c->ncls, c->matsh, cabd, c->coef, 0) == cudaSuccess &&
-         cudaDeviceSynchronize() == cudaSuccess;
+         build_coef_tables(c->kvar, c->nmat, c->ncls, c->matsh, cabd, c->coef, 0) == cudaSuccess;
+    if (ok) {
+      add_launches(1);
+      material_kernel<<<(unsigned)((nx + 255) / 256), 256>>>(nx, h, c->d64.sigt, c->matsh, c->nmat, c->mat);
+      ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    }
     cudaFree(cabd);
     if (!ok) {   // no tables: the FP64 sweeps compute the coefficients themselves
       cudaGetLastError();

@@ -433,6 +433,8 @@ void dsa_free(VertexDsa &d) {
   }
   cudaFree(d.cinv);
   d.cinv = nullptr;
+  if (d.vcycle_graph) cudaGraphExecDestroy(d.vcycle_graph);
+  d.vcycle_graph = nullptr;
   d.nlev = -1;
 }
 
@@ -498,7 +500,27 @@ int dsa_build(VertexDsa &d, int avg, int ni, int nj, double h, double eps, const
     if (cudaMemcpyAsync(d.cinv, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return LMDG_ERR_CUDA;
   }
-  return cudaStreamSynchronize(s) == cudaSuccess ? 0 : LMDG_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LMDG_ERR_CUDA;
+  // The V-cycle is the same sequence of about 7 launches per level on fixed buffers (lev[0].b in, lev[0].x out)
+  // every time: capture it once on a private stream and replay it as one graph launch, so the coarse levels' tiny
+  // kernels do not each pay a launch.  If capture is not available the cycle is launched kernel by kernel.
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+    cudaGraph_t g = nullptr;
+    const long long l0 = launch_count();
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const cudaError_t ev = vcycle(d, 0, cs);
+      ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && ev == cudaSuccess && g != nullptr;
+    }
+    d.vcycle_launches = launch_count() - l0;
+    add_launches(-d.vcycle_launches);          // counted when replayed
+    if (ok && cudaGraphInstantiate(&d.vcycle_graph, g, 0) != cudaSuccess) d.vcycle_graph = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();                        // a refused capture leaves no error behind: the fallback runs
+  }
+  return 0;
 }
 
 cudaError_t dsa_apply(const VertexDsa &d, int ni, int nj, double h, const double *sse, int lowmem, double *u,
@@ -508,7 +530,12 @@ cudaError_t dsa_apply(const VertexDsa &d, int ni, int nj, double h, const double
   load_kernel<<<grid_of((long long)nvert(L0)), kBlock, 0, s>>>(ni, nj, h, sse, u, lowmem, L0.b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = vcycle(d, 0, s)) != cudaSuccess) return e;   // one V-cycle from zero
+  if (d.vcycle_graph) {                                 // one V-cycle from zero
+    add_launches(d.vcycle_launches);
+    if ((e = cudaGraphLaunch(d.vcycle_graph, s)) != cudaSuccess) return e;
+  } else if ((e = vcycle(d, 0, s)) != cudaSuccess) {
+    return e;
+  }
   add_launches(1);
   interp_add_kernel<<<grid_of((long long)ni * nj), kBlock, 0, s>>>(ni, nj, L0.x, lowmem, u);
   return cudaGetLastError();

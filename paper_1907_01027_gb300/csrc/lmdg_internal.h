@@ -98,6 +98,8 @@ struct VertexDsa {
   double *cinv = nullptr;          // dense inverse of the coarsest matrix, or null (then coarse_sweeps Jacobi steps)
   int nu = 2, coarse_sweeps = 50;  // smoothing steps before and after the coarse correction; coarsest fallback
   double omega = 0.7;              // damping of the block-Jacobi smoother
+  cudaGraphExec_t vcycle_graph = nullptr;   // the V-cycle's launches captured once (null: launched one by one)
+  long long vcycle_launches = 0;   // kernels in the captured V-cycle
 };
 // Build the hierarchy for ni x nj cells (sigt, sigma_a per cell, device; Ax, Ay the half-range outflow weights):
 // 0 or an LMDG_ERR_* code.  Synchronises s.
@@ -167,7 +169,8 @@ struct lmdg_ctx {
   double Ax[2] = {0, 0}, Ay[2] = {0, 0};   // sum of w |Omega_x| over Omega_x > 0 / < 0, likewise y
   double *qmom = nullptr;                  // device [5] quadrature moments (epilogue)
   lmdg::SweepGeom g64{}, g32{}, g2{};
-  void *part = nullptr;                    // partial reductions (double-sized)
+  void *part = nullptr;                    // partial reductions, grown to the largest launch shape used
+  size_t part_bytes = 0;
   void *ytr = nullptr;                     // inter-strip traces (double-sized)
   void *cellsrc = nullptr;                 // [nx][4] per-sweep cell inputs (double-sized)
   void *cellsh = nullptr;                  // [nx]
@@ -177,7 +180,8 @@ struct lmdg_ctx {
   bool ytr_dirty = true;                   // ytr must be refilled with kTraceEmpty before the next sweep
   int ytr_prec = -1;                       // trace layout of the last sweep using ytr (0: 8-byte, 1: 4-byte)
   int part_prec = -1;                      // arithmetic (0 double, 1 float, 2 float-float) of the last partials
-  void *psi = nullptr;                     // stored angular unknowns
+  void *psi = nullptr;                     // stored angular unknowns, grown to the widest kind stored
+  size_t psi_bytes = 0;
   int psi_kind = -1;                       // -1 none, 0 double, 1 float, 2 bf16
   size_t psi_elems = 0;
   // Krylov workspace
