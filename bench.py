@@ -38,12 +38,12 @@ FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 # partial reductions per cell, is the same at 1024x1024, so a full launch moves 4x these), issue-active % of the
 # schedulers, warps active % of the maximum, and warp instructions per cell-direction update.  None until measured
 # for the current kernels; must be re-measured whenever the kernel changes.
-SWEEP_NCU_512 = {"std": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
-                         "inst_per_update": None},
-                 "lm": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
-                        "inst_per_update": None},
-                 "rlm": {"dram_bytes": None, "issue_active_pct": None, "warps_active_pct": None,
-                         "inst_per_update": None}}
+SWEEP_NCU_512 = {"std": {"dram_bytes": 68.402688e6, "issue_active_pct": 43.14, "warps_active_pct": 23.97,
+                         "inst_per_update": 4.995},
+                 "lm": {"dram_bytes": 35.471616e6, "issue_active_pct": 23.42, "warps_active_pct": 11.78,
+                        "inst_per_update": 2.637},
+                 "rlm": {"dram_bytes": 109.411584e6, "issue_active_pct": 38.51, "warps_active_pct": 23.91,
+                         "inst_per_update": 5.945}}
 # the pipeline of the sweep: a strip of 32 rows takes n + 31 steps and the strip above starts 32 + 8 steps later
 STRIP_LAG = 40
 

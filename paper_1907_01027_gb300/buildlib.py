@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblmdg.so")
-UNITS = ["sweep.cu", "krylov.cu", "api.cu", "noalloc.cu", "geom.cu", "dsa.cu"]
+UNITS = ["sweep.cu", "krylov.cu", "api.cu", "noalloc.cu", "geom.cu", "dsa.cu", "mem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
          "--expt-relaxed-constexpr"]

@@ -27,7 +27,7 @@ int quadrant(double ox, double oy) { return oy > 0 ? (ox > 0 ? 0 : 1) : (ox < 0 
 // n host doubles to a new device array of T (converted on the host when T is not double)
 template <typename T>
 int upload(T **dst, const double *src, size_t n) {
-  if (cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, n)) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (lmdg::dmalloc(dst, sizeof(T) * std::max<size_t>(1, n)) != cudaSuccess) return LMDG_ERR_NOMEM;
   if (n == 0) return 0;
   if constexpr (std::is_same<T, double>::value) {
     CK(cudaMemcpy(*dst, src, sizeof(double) * n, cudaMemcpyHostToDevice));
@@ -44,8 +44,8 @@ int upload(T **dst, const std::vector<double> &src) {
 
 template <typename T>
 void free_pd(ProblemData<T> &p) {
-  cudaFree(p.ox); cudaFree(p.oy); cudaFree(p.w); cudaFree(p.sigt); cudaFree(p.sse); cudaFree(p.q);
-  cudaFree(p.alpha);
+  lmdg::dfree(p.ox); lmdg::dfree(p.oy); lmdg::dfree(p.w); lmdg::dfree(p.sigt); lmdg::dfree(p.sse); lmdg::dfree(p.q);
+  lmdg::dfree(p.alpha);
   p = ProblemData<T>();
 }
 
@@ -75,7 +75,7 @@ int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
   // a failed allocation leaves the arrays made so far in place (freed by lmdg_destroy) for the next attempt
   for (auto &it : items) {
     if (it.n == 0 || it.src == nullptr) continue;
-    if (*it.dst == nullptr && cudaMalloc(it.dst, sizeof(f2) * it.n) != cudaSuccess) {
+    if (*it.dst == nullptr && lmdg::dmalloc(it.dst, sizeof(f2) * it.n) != cudaSuccess) {
       *it.dst = nullptr;
       return LMDG_ERR_NOMEM;
     }
@@ -107,10 +107,10 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     // partial reductions of this launch shape and arithmetic: the buffer grows to the largest one used
     const size_t pbytes = (size_t)4 * a.g.groups * c->nx * nr_of(c->kvar) * sizeof(T);
     if (c->part_bytes < pbytes) {
-      cudaFree(c->part);
+      lmdg::dfree(c->part);
       c->part = nullptr;
       c->part_bytes = 0;
-      if (cudaMalloc(&c->part, pbytes) != cudaSuccess) { c->part = nullptr; return LMDG_ERR_NOMEM; }
+      if (lmdg::dmalloc(&c->part, pbytes) != cudaSuccess) { c->part = nullptr; return LMDG_ERR_NOMEM; }
       c->part_bytes = pbytes;
     }
   }
@@ -151,11 +151,11 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     size_t elems = (size_t)c->nang * c->nx * per;
     const size_t bytes = elems * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
     if (c->psi_bytes < bytes) {   // grown to the widest kind stored so far (cudaFree waits for earlier use)
-      cudaFree(c->psi);
+      lmdg::dfree(c->psi);
       c->psi = nullptr;
       c->psi_bytes = 0;
       c->psi_kind = -1;
-      if (cudaMalloc(&c->psi, bytes) != cudaSuccess) { c->psi = nullptr; return LMDG_ERR_NOMEM; }
+      if (lmdg::dmalloc(&c->psi, bytes) != cudaSuccess) { c->psi = nullptr; return LMDG_ERR_NOMEM; }
       c->psi_bytes = bytes;
     }
     c->psi_kind = kind;
@@ -247,16 +247,16 @@ cudaError_t launch_phi(lmdg_ctx *c, const T *part, int Pn, const double *X, doub
 int ensure_krylov(lmdg_ctx *c, int m) {
   const size_t N = 4 * (size_t)c->nx;
   if (c->V && c->red_len >= m + 2) return 0;
-  cudaFree(c->V);
-  for (auto &v : c->vec) { cudaFree(v); v = nullptr; }
-  cudaFree(c->red);
+  lmdg::dfree(c->V);
+  for (auto &v : c->vec) { lmdg::dfree(v); v = nullptr; }
+  lmdg::dfree(c->red);
   if (c->red_h) cudaFreeHost(c->red_h);
   c->V = nullptr; c->red = nullptr; c->red_h = nullptr;
-  if (cudaMalloc(&c->V, sizeof(double) * N * (m + 1)) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (lmdg::dmalloc(&c->V, sizeof(double) * N * (m + 1)) != cudaSuccess) return LMDG_ERR_NOMEM;
   for (auto &v : c->vec)
-    if (cudaMalloc(&v, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&v, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
   size_t rl = mdot_partial_len(m + 2) + 4 * (size_t)(m + 2);
-  if (cudaMalloc(&c->red, sizeof(double) * rl) != cudaSuccess) return LMDG_ERR_NOMEM;
+  if (lmdg::dmalloc(&c->red, sizeof(double) * rl) != cudaSuccess) return LMDG_ERR_NOMEM;
   if (cudaMallocHost(&c->red_h, sizeof(double) * 4 * (m + 2)) != cudaSuccess) return LMDG_ERR_NOMEM;
   c->red_len = m + 2;
   return 0;
@@ -504,16 +504,17 @@ void lmdg_destroy(lmdg_ctx *c) {
   free_pd(c->d64);
   free_pd(c->d32);
   free_pd(c->d2);
-  cudaFree(c->p1ra2); cudaFree(c->coef2); cudaFree(c->qadj2);
-  cudaFree(c->perm); cudaFree(c->p1ra64); cudaFree(c->p1ra32); cudaFree(c->sq1); cudaFree(c->b11dinv);
-  cudaFree(c->sigma_a); cudaFree(c->qmom); cudaFree(c->part); cudaFree(c->ytr); cudaFree(c->ctrl); cudaFree(c->psi);
-  cudaFree(c->cellsrc); cudaFree(c->cellsh);
-  cudaFree(c->rev); cudaFree(c->qadj64); cudaFree(c->qadj32); cudaFree(c->adj_buf);
-  cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh); cudaFree(c->coef); cudaFree(c->supp);
+  lmdg::dfree(c->p1ra2); lmdg::dfree(c->coef2); lmdg::dfree(c->qadj2);
+  lmdg::dfree(c->perm); lmdg::dfree(c->p1ra64); lmdg::dfree(c->p1ra32); lmdg::dfree(c->sq1); lmdg::dfree(c->b11dinv);
+  lmdg::dfree(c->sigma_a); lmdg::dfree(c->qmom); lmdg::dfree(c->part); lmdg::dfree(c->ytr); lmdg::dfree(c->ctrl);
+  lmdg::dfree(c->psi);
+  lmdg::dfree(c->cellsrc); lmdg::dfree(c->cellsh);
+  lmdg::dfree(c->rev); lmdg::dfree(c->qadj64); lmdg::dfree(c->qadj32); lmdg::dfree(c->adj_buf);
+  lmdg::dfree(c->mat); lmdg::dfree(c->cls); lmdg::dfree(c->matsh); lmdg::dfree(c->coef); lmdg::dfree(c->supp);
   lmdg::dsa_free(c->dsa);
-  cudaFree(c->V);
-  for (auto &v : c->vec) cudaFree(v);
-  cudaFree(c->red);
+  lmdg::dfree(c->V);
+  for (auto &v : c->vec) lmdg::dfree(v);
+  lmdg::dfree(c->red);
   if (c->red_h) cudaFreeHost(c->red_h);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -697,8 +698,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   c->rev_ok = rev_ok;
   phase("host tables");
   int e = 0;
-  if (cudaMalloc(&c->perm, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
-  if (cudaMalloc(&c->rev, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->perm, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->rev, sizeof(int) * na) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemcpy(c->rev, rev.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LMDG_ERR_CUDA);
   if (cudaMemcpy(c->perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -710,25 +711,25 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       (e = upload(&c->d32.ox, ox)) || (e = upload(&c->d32.oy, oy)) || (e = upload(&c->d32.w, w)) ||
       (e = upload(&ss_dev, sigma_s, nx)) || (e = upload(&c->sigma_a, sigma_a, nx)) || (e = upload(&c->qmom, qm)) ||
       (q_layout == 0 && (e = upload(&q0_dev, qsrc, qn)))) {
-    cudaFree(ss_dev);
-    cudaFree(q0_dev);
+    lmdg::dfree(ss_dev);
+    lmdg::dfree(q0_dev);
     return fail(e);
   }
-  if ((q_layout == 0 && cudaMalloc(&c->d64.q, sizeof(double) * nq4) != cudaSuccess) ||
+  if ((q_layout == 0 && lmdg::dmalloc(&c->d64.q, sizeof(double) * nq4) != cudaSuccess) ||
       (q_layout != 0 && (e = upload(&c->d64.q, qsrc, qn)))) {
-    cudaFree(ss_dev);
-    cudaFree(q0_dev);
+    lmdg::dfree(ss_dev);
+    lmdg::dfree(q0_dev);
     return fail(e ? e : LMDG_ERR_NOMEM);
   }
-  bool ok = cudaMalloc(&c->d64.sigt, sizeof(double) * nx) == cudaSuccess &&
-            cudaMalloc(&c->d64.sse, sizeof(double) * nx) == cudaSuccess &&
-            cudaMalloc(&c->d32.sigt, sizeof(float) * nx) == cudaSuccess &&
-            cudaMalloc(&c->d32.sse, sizeof(float) * nx) == cudaSuccess &&
-            cudaMalloc(&c->d32.q, sizeof(float) * nq4) == cudaSuccess &&
-            cudaMalloc(&c->sq1, sizeof(double) * 3 * nx) == cudaSuccess &&
-            cudaMalloc(&c->p1ra64, sizeof(double) * 3 * nx) == cudaSuccess &&
-            cudaMalloc(&c->p1ra32, sizeof(float) * 3 * nx) == cudaSuccess &&
-            cudaMalloc(&c->b11dinv, sizeof(double) * 3 * nx) == cudaSuccess;
+  bool ok = lmdg::dmalloc(&c->d64.sigt, sizeof(double) * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->d64.sse, sizeof(double) * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->d32.sigt, sizeof(float) * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->d32.sse, sizeof(float) * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->d32.q, sizeof(float) * nq4) == cudaSuccess &&
+            lmdg::dmalloc(&c->sq1, sizeof(double) * 3 * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->p1ra64, sizeof(double) * 3 * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->p1ra32, sizeof(float) * 3 * nx) == cudaSuccess &&
+            lmdg::dmalloc(&c->b11dinv, sizeof(double) * 3 * nx) == cudaSuccess;
   if (ok) {
     add_launches(1);
     cell_tables_kernel<<<(unsigned)((nx + 255) / 256), 256>>>(
@@ -740,7 +741,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (ok && q_layout == 2) ok = to_float(c->d64.q, c->d32.q, nq4, 0) == cudaSuccess;
   if (ok && alpha) {
     double *bnd_dev = nullptr;
-    if ((e = upload(&bnd_dev, bnd))) { cudaFree(ss_dev); cudaFree(q0_dev); return fail(e); }
+    if ((e = upload(&bnd_dev, bnd))) { lmdg::dfree(ss_dev); lmdg::dfree(q0_dev); return fail(e); }
     for (int side = 0; side < 4 && ok; ++side) {   // one side per launch: a corner cell has faces on two sides
       const int count = side < 2 ? nj : ni;
       add_launches(1);
@@ -748,12 +749,12 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       ok = cudaGetLastError() == cudaSuccess;
     }
     ok = ok && cudaDeviceSynchronize() == cudaSuccess;
-    cudaFree(bnd_dev);
+    lmdg::dfree(bnd_dev);
   }
   if (ok) ok = to_float(c->p1ra64, c->p1ra32, 3 * nx, 0) == cudaSuccess;
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
-  cudaFree(ss_dev);
-  cudaFree(q0_dev);
+  lmdg::dfree(ss_dev);
+  lmdg::dfree(q0_dev);
   if (!ok) return fail(LMDG_ERR_CUDA);
   if (alpha) {
     if ((e = upload(&c->d64.alpha, av)) || (e = upload(&c->d32.alpha, av))) return fail(e);
@@ -787,13 +788,13 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
                  c->g2.apw);
   const int strips = (nj + 31) / 32;
   const size_t ytr_elems = (size_t)na * strips * ni * kTraceStride;
-  if (cudaMalloc(&c->ytr, sizeof(double) * ytr_elems) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->ytr, sizeof(double) * ytr_elems) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   c->ytr_words = 2 * ytr_elems;
   c->ytr_dirty = true;
-  if (cudaMalloc(&c->cellsrc, sizeof(double) * 4 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
-  if (cudaMalloc(&c->cellsh, sizeof(double) * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->cellsrc, sizeof(double) * 4 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->cellsh, sizeof(double) * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   c->ctrl_words = 2 + (size_t)std::max({c->g64.units(), c->g32.units(), c->g2.units()});
-  if (cudaMalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+  if (lmdg::dmalloc(&c->ctrl, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
   if (cudaMemset(c->ctrl, 0, sizeof(unsigned) * c->ctrl_words) != cudaSuccess) return fail(LMDG_ERR_CUDA);
   phase("work buffers");
   // FP64 element-solve coefficient tables per (material = distinct sigma_t h, direction class = distinct
@@ -825,10 +826,11 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     c->ncoef = coef_count(c->kvar);
     const size_t tbytes = sizeof(double) * (size_t)c->nmat * c->ncls * c->ncoef;
     double *cabd = nullptr;
-    bool ok = cudaMalloc(&c->coef, tbytes) == cudaSuccess && cudaMalloc(&c->mat, sizeof(int) * nx) == cudaSuccess &&
-              cudaMalloc(&c->cls, sizeof(int) * na) == cudaSuccess &&
-              cudaMalloc(&c->matsh, sizeof(double) * c->nmat) == cudaSuccess &&
-              cudaMalloc(&cabd, sizeof(double) * cab.size()) == cudaSuccess;
+    bool ok = lmdg::dmalloc(&c->coef, tbytes) == cudaSuccess &&
+              lmdg::dmalloc(&c->mat, sizeof(int) * nx) == cudaSuccess &&
+              lmdg::dmalloc(&c->cls, sizeof(int) * na) == cudaSuccess &&
+              lmdg::dmalloc(&c->matsh, sizeof(double) * c->nmat) == cudaSuccess &&
+              lmdg::dmalloc(&cabd, sizeof(double) * cab.size()) == cudaSuccess;
     ok = ok && cudaMemcpy(c->cls, clsv.data(), sizeof(int) * na, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(c->matsh, uniq.data(), sizeof(double) * c->nmat, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(cabd, cab.data(), sizeof(double) * cab.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -838,10 +840,10 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       material_kernel<<<(unsigned)((nx + 255) / 256), 256>>>(nx, h, c->d64.sigt, c->matsh, c->nmat, c->mat);
       ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
     }
-    cudaFree(cabd);
+    lmdg::dfree(cabd);
     if (!ok) {   // no tables: the FP64 sweeps compute the coefficients themselves
       cudaGetLastError();
-      cudaFree(c->coef); cudaFree(c->mat); cudaFree(c->cls); cudaFree(c->matsh);
+      lmdg::dfree(c->coef); lmdg::dfree(c->mat); lmdg::dfree(c->cls); lmdg::dfree(c->matsh);
       c->coef = nullptr; c->mat = nullptr; c->cls = nullptr; c->matsh = nullptr;
     }
   }
@@ -890,11 +892,11 @@ int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   CK(cudaSetDevice(c->dev));
   if (flags & LMDG_HOST_PTRS) {
     double *tmp = nullptr;
-    if (cudaMalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
     cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s);
     cudaError_t e2 = cudaMemcpyAsync(psi, tmp, sizeof(double) * c->psi_elems, cudaMemcpyDeviceToHost, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
-    cudaFree(tmp);
+    lmdg::dfree(tmp);
     return (e1 || e2 || e3) ? LMDG_ERR_CUDA : 0;
   }
   CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s));
@@ -1097,10 +1099,10 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
   const size_t nx = (size_t)c->nx, N = 4 * nx;
   const bool host = (flags & LMDG_HOST_PTRS) != 0;
   if (!c->adj_buf) {
-    if (cudaMalloc(&c->adj_buf, sizeof(double) * (5 * N + 4 * nx)) != cudaSuccess) return LMDG_ERR_NOMEM;
-    if (cudaMalloc(&c->qadj64, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
-    if (cudaMalloc(&c->qadj32, sizeof(float) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
-    if (cudaMalloc(&c->qadj2, sizeof(f2) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&c->adj_buf, sizeof(double) * (5 * N + 4 * nx)) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&c->qadj64, sizeof(double) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&c->qadj32, sizeof(float) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&c->qadj2, sizeof(f2) * N) != cudaSuccess) return LMDG_ERR_NOMEM;
   }
   double *Xf = c->adj_buf, *Lam = c->adj_buf + N, *Y = c->adj_buf + 2 * N, *G = c->adj_buf + 3 * N;
   double *PhiF = c->adj_buf + 3 * N + 4 * nx, *PhiA = PhiF + N;   // scalar-flux moments (low-memory)

@@ -428,10 +428,10 @@ cudaError_t vcycle(const VertexDsa &d, int l, cudaStream_t s) {
 
 void dsa_free(VertexDsa &d) {
   for (auto &L : d.lev) {
-    cudaFree(L.A); cudaFree(L.dinv); cudaFree(L.x); cudaFree(L.y); cudaFree(L.b); cudaFree(L.r);
+    lmdg::dfree(L.A); lmdg::dfree(L.dinv); lmdg::dfree(L.x); lmdg::dfree(L.y); lmdg::dfree(L.b); lmdg::dfree(L.r);
     L = MgLevel();
   }
-  cudaFree(d.cinv);
+  lmdg::dfree(d.cinv);
   d.cinv = nullptr;
   if (d.vcycle_graph) cudaGraphExecDestroy(d.vcycle_graph);
   d.vcycle_graph = nullptr;
@@ -448,12 +448,12 @@ int dsa_build(VertexDsa &d, int avg, int ni, int nj, double h, double eps, const
     MgLevel &L = d.lev[nl];
     L.ni = ci; L.nj = cj; L.bs = bs;
     const size_t nv = nvert(L);
-    if (cudaMalloc(&L.A, sizeof(double) * nv * 9 * bs * bs) != cudaSuccess ||
-        cudaMalloc(&L.dinv, sizeof(double) * nv * bs * bs) != cudaSuccess ||
-        cudaMalloc(&L.x, sizeof(double) * nv * bs) != cudaSuccess ||
-        cudaMalloc(&L.y, sizeof(double) * nv * bs) != cudaSuccess ||
-        cudaMalloc(&L.b, sizeof(double) * nv * bs) != cudaSuccess ||
-        cudaMalloc(&L.r, sizeof(double) * nv * bs) != cudaSuccess)
+    if (lmdg::dmalloc(&L.A, sizeof(double) * nv * 9 * bs * bs) != cudaSuccess ||
+        lmdg::dmalloc(&L.dinv, sizeof(double) * nv * bs * bs) != cudaSuccess ||
+        lmdg::dmalloc(&L.x, sizeof(double) * nv * bs) != cudaSuccess ||
+        lmdg::dmalloc(&L.y, sizeof(double) * nv * bs) != cudaSuccess ||
+        lmdg::dmalloc(&L.b, sizeof(double) * nv * bs) != cudaSuccess ||
+        lmdg::dmalloc(&L.r, sizeof(double) * nv * bs) != cudaSuccess)
       return LMDG_ERR_NOMEM;
     const int gv = grid_of((long long)nv);
     add_launches(2);
@@ -496,7 +496,7 @@ int dsa_build(VertexDsa &d, int avg, int ni, int nj, double h, double eps, const
       }
     }
     if (!dense_inverse(M, N)) return LMDG_ERR_BREAKDOWN;
-    if (cudaMalloc(&d.cinv, sizeof(double) * M.size()) != cudaSuccess) return LMDG_ERR_NOMEM;
+    if (lmdg::dmalloc(&d.cinv, sizeof(double) * M.size()) != cudaSuccess) return LMDG_ERR_NOMEM;
     if (cudaMemcpyAsync(d.cinv, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return LMDG_ERR_CUDA;
   }

@@ -111,6 +111,15 @@ void dsa_free(VertexDsa &d);
 cudaError_t dsa_apply(const VertexDsa &d, int ni, int nj, double h, const double *sse, int lowmem, double *u,
                       cudaStream_t s);
 
+// Device memory of the contexts (mem.cu): allocations from a per-device pool that keeps freed memory mapped for the
+// next context; dalloc returns memory usable on any stream, dfree waits for the device before returning it.
+cudaError_t dalloc(void **p, size_t bytes);
+template <typename T>
+cudaError_t dmalloc(T **p, size_t bytes) {
+  return dalloc(reinterpret_cast<void **>(p), bytes);
+}
+void dfree(void *p);
+
 // Number of kernels launched by this library (all host wrappers add to it).
 long long launch_count();
 void add_launches(long long k);
