@@ -55,8 +55,10 @@ enum {
   LMDG_SWEEP_FP32 = 2,     /* run the sweep in float (x, y stay double) */
   LMDG_SWEEP_STORE = 4,    /* also store the angular unknowns of this sweep in the context (see lmdg_get_psi) */
   LMDG_HOST_PTRS = 8,      /* x, y (and other vectors of the call) are host pointers */
-  LMDG_SWEEP_F32X2 = 16    /* run the sweep in float-float (see LMDG_RESID_F32X2); not with LMDG_SWEEP_FP32 or
+  LMDG_SWEEP_F32X2 = 16,   /* run the sweep in float-float (see LMDG_RESID_F32X2); not with LMDG_SWEEP_FP32 or
                               LMDG_SWEEP_STORE */
+  LMDG_SOLVE_EXACT_REF = 32 /* lmdg_solve, FP32 modes started from zero: take b and the tolerance reference ||b||
+                              from a sweep in the residual arithmetic instead of an FP32 sweep (see lmdg_solve) */
 };
 
 /* Errors */
@@ -121,8 +123,9 @@ typedef struct {
   int refinements;     /* outer FP64 refinement steps (FP32 modes), 0 for FP64 */
   int sweeps_fp64;     /* full transport sweeps run in FP64 */
   int sweeps_fp32;     /* full transport sweeps run in FP32 */
-  double resid0;       /* reference norm: ||r_0|| = ||b - K x0|| (FP64), or ||b|| from an FP32 sweep when an
-                          FP32 mode starts from zero */
+  double resid0;       /* tolerance reference ||b - K x0|| (||b|| when starting from zero): from a sweep in the
+                          residual arithmetic, or from an FP32 sweep in the FP32 modes started from zero without
+                          LMDG_SOLVE_EXACT_REF */
   double resid;        /* final ||b - K x|| from a residual sweep (FP64, or float-float with LMDG_RESID_F32X2) */
   double time_ms;      /* wall time of the call (host clock) */
   double sweep_ms_fp64;/* device time inside FP64 sweep kernels (CUDA events around each launch) */
@@ -177,8 +180,14 @@ int lmdg_sweep(lmdg_ctx *ctx, const double *x, double *y, int flags, void *strea
 /* Solve the reduced system with restarted GMRES (right-preconditioned, see lmdg_options.precond), then run
  * the recovery sweep (eq-sndg-final-sweep, eq-lm-step4 and its RLMDG analogue), storing the angular unknowns.
  * FP32 modes: the first iterate comes from FP32 sweeps alone (an FP32 right-hand side and one FP32 GMRES
- * cycle); every later step computes the residual b - K x with an FP64 sweep, runs FP32-sweep GMRES on it and
- * updates x in FP64 (iterative refinement).  Convergence is ||b - K x|| <= tol ||b|| on FP64 residuals.
+ * cycle); every later step computes the residual b - K x with a sweep in the residual arithmetic (FP64, or
+ * float-float with LMDG_RESID_F32X2), runs FP32-sweep GMRES on it and updates x in FP64 (iterative
+ * refinement).  Convergence is ||b - K x|| <= tol ||b||, the residual in the residual arithmetic.  The reference
+ * ||b||: from x0 = 0 in the FP32 modes it is the norm of the FP32 right-hand side, which differs from the exact
+ * ||b|| by the FP32 sweep's normwise relative error (below 1e-5 on the tested problems), so the relative residual
+ * reached is tol (1 + that error); with LMDG_SOLVE_EXACT_REF in flags b comes from a residual-arithmetic sweep
+ * instead (one such sweep in place of an FP32 one) and the bound is tol itself.  With x0 given, or in FP64, the
+ * reference is ||b - K x0|| from a residual-arithmetic sweep.
  *   x0  : initial guess [N][4] (NULL = zero), in the unknowns of lmdg_sweep with LMDG_SWEEP_SOURCE.
  *   x   : output [N][4], the converged unknowns (may be NULL).
  *   phi : output [N][4], the scalar-flux moments sum_l w_l psi_l of the discrete solution (may be NULL).

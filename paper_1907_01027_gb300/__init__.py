@@ -5,8 +5,8 @@ is a thin ctypes binding over it.  There is no CPU fallback: importing :mod:`.lm
 not built.
 """
 from .lmdg import (Context, LmdgError, build, STD, LM, RLM, P0, FP64, FP32, FP32_BF16STORE, SWEEP_SOURCE,
-                   SWEEP_FP32, SWEEP_STORE, SWEEP_F32X2, HOST_PTRS, RESID_FP64, RESID_F32X2, VARIANTS)
+                   SWEEP_FP32, SWEEP_STORE, SWEEP_F32X2, SOLVE_EXACT_REF, HOST_PTRS, RESID_FP64, RESID_F32X2, VARIANTS)
 
 __all__ = ["Context", "LmdgError", "build", "STD", "LM", "RLM", "P0", "FP64", "FP32", "FP32_BF16STORE",
-           "SWEEP_SOURCE", "SWEEP_FP32", "SWEEP_STORE", "SWEEP_F32X2", "HOST_PTRS", "RESID_FP64", "RESID_F32X2",
+           "SWEEP_SOURCE", "SWEEP_FP32", "SWEEP_STORE", "SWEEP_F32X2", "SOLVE_EXACT_REF", "HOST_PTRS", "RESID_FP64", "RESID_F32X2",
            "VARIANTS"]

@@ -934,12 +934,17 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
   int iters = 0, refine = 0, status = 0;
   double r0 = 0;
   if (fp32 && !x0) {
-    // FP32 start: b from an FP32 source sweep (||b|| is the tolerance reference) and an FP32 GMRES cycle for
-    // the first iterate, so that the FP64 sweeps are spent only on residuals at iterates
-    if (int e = sweep_prec(c, 1, X, R, 1, false, 0, s)) return e;   // X = 0: R = K 0 - b = -b
-    CK(axpby(R, -1.0, R, 0.0, N, s));
-    if (int e = check_error_word(c, s)) return e;
-    if (int e = norm2(c, R, &rn2, s)) return e;
+    // FP32 start from zero: b from an FP32 source sweep (or, with LMDG_SOLVE_EXACT_REF, from a sweep in the
+    // residual arithmetic, so that the tolerance reference ||b|| carries no FP32 error) and an FP32 GMRES cycle
+    // for the first iterate; the residual-arithmetic sweeps are then spent only on residuals at iterates
+    if (flags & LMDG_SOLVE_EXACT_REF) {
+      if (int e = residual(&rn2)) return e;                          // X = 0: R = b
+    } else {
+      if (int e = sweep_prec(c, 1, X, R, 1, false, 0, s)) return e;   // X = 0: R = K 0 - b = -b
+      CK(axpby(R, -1.0, R, 0.0, N, s));
+      if (int e = check_error_word(c, s)) return e;
+      if (int e = norm2(c, R, &rn2, s)) return e;
+    }
     r0 = std::sqrt(rn2);
     if (!std::isfinite(r0)) return LMDG_ERR_BREAKDOWN;
     if (r0 > 0) {

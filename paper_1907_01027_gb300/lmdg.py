@@ -13,7 +13,7 @@ from . import buildlib as _build_mod
 STD, LM, RLM, P0 = 0, 1, 2, 3
 VARIANTS = {"std": STD, "lm": LM, "rlm": RLM, "p0": P0}
 FP64, FP32, FP32_BF16STORE = 0, 1, 2
-SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS, SWEEP_F32X2 = 1, 2, 4, 8, 16
+SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS, SWEEP_F32X2, SOLVE_EXACT_REF = 1, 2, 4, 8, 16, 32
 RESID_FP64, RESID_F32X2 = 0, 1
 ERR_TIMEOUT, ERR_NOTCONV, ERR_BREAKDOWN = -6, -5, -7
 
@@ -176,25 +176,26 @@ class Context:
         self._check(rc, "lmdg_sweep")
         return y
 
-    def solve(self, x0=None, want_x=True, want_phi=True, device=False, allow_stall=False):
+    def solve(self, x0=None, want_x=True, want_phi=True, device=False, allow_stall=False, exact_ref=False):
         """lmdg_solve.  Returns (x, phi, stats dict, status).  LMDG_ERR_NOTCONV returns normally (outputs written);
         with ``allow_stall`` so does LMDG_ERR_BREAKDOWN from a residual that stopped decreasing (a solve driven
-        below what the arithmetic can reach)."""
+        below what the arithmetic can reach).  ``exact_ref``: LMDG_SOLVE_EXACT_REF."""
         st = Stats()
+        fl = SOLVE_EXACT_REF if exact_ref else 0
         if device:
             import torch
             x = torch.empty((self.nx, 4), dtype=torch.float64, device="cuda") if want_x else None
             phi = torch.empty((self.nx, 4), dtype=torch.float64, device="cuda") if want_phi else None
             rc = self.lib.lmdg_solve(self.h, None if x0 is None else x0.data_ptr(),
                                      None if x is None else x.data_ptr(), None if phi is None else phi.data_ptr(),
-                                     ctypes.byref(st), 0, _stream())
+                                     ctypes.byref(st), fl, _stream())
         else:
             x = np.empty((self.nx, 4)) if want_x else None
             phi = np.empty((self.nx, 4)) if want_phi else None
             x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
             rc = self.lib.lmdg_solve(self.h, None if x0a is None else x0a.ctypes.data,
                                      None if x is None else x.ctypes.data, None if phi is None else phi.ctypes.data,
-                                     ctypes.byref(st), HOST_PTRS, None)
+                                     ctypes.byref(st), HOST_PTRS | fl, None)
         self._check(rc, "lmdg_solve", allow=(ERR_NOTCONV, ERR_BREAKDOWN) if allow_stall else (ERR_NOTCONV,))
         return x, phi, st.as_dict(), rc
 

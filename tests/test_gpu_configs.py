@@ -1,0 +1,111 @@
+"""The workload configurations that are not the benchmark's own, as parity cases on the GPU.
+
+* 32^2 cells, S4, sigma_s = 1, sigma_a = 0.5 (the small FP64 case): every scheme's solve driven to stagnation
+  against the oracle's solve: its GMRES to 1e-14 for Q1-DG (condition number 1.6, so that is the exact solution
+  to about 1e-14), its direct (LU) solve for LMDG and RLMDG.  Two FP64 solutions of a system with condition
+  number kappa differ by up to about kappa times the rounding of the operator (a few 1e-16): 1e-12 for Q1-DG, and
+  3e-11 for LMDG and RLMDG, whose reduced operators have kappa = 1.3e4 and 1.4e4 here.
+* 256^2 cells, S8, sigma_s = sigma_a = 1, eps in {1, 1e-2, 1e-4} (the diffusion-limit sweep): Q1-DG and LMDG
+  solves with the vertex diffusion correction to 1e-8, each certified by the oracle: the oracle's reduced
+  operator applied to the GPU's solution leaves a residual within the solve's tolerance.  (At eps = 1e-4 the
+  reduced operator's smallest eigenvalues are of order eps^2, and the FP64 residual of an exact solution is
+  itself near 1e-9 of |b|: 1e-8 is the tolerance FP64 reaches there.)
+* 512^2 cells, S12, the 7x7 block pattern of absorbing blocks (sigma_s = 0, sigma_a = 10) in a pure scatterer,
+  source in the centre block (the RLMDG case): the FP64 RLMDG operator application against the oracle at
+  1e-12, the FP64 solve certified by the oracle's residual, and the mixed-precision solve certified by the
+  FP64 operator (itself at 1e-12 of the oracle's).
+
+The GPU's low-memory unknowns are (X0, X1) with the first-moment unknowns offset by the source term z of the
+reduced system (Phi1 = z - X1), so the oracle's unknowns are x + e, e = (0, z); the residual of the oracle's
+system at the GPU's solution is K(x + e) - b.
+"""
+import numpy as np
+import pytest
+
+from oracle.sweeps import SweepOracle
+from tests.helpers import rel
+from workloads.problems import config1, config2, config3
+
+pytestmark = pytest.mark.gpu
+
+
+def _offset(so, variant):
+    e = np.zeros((so.nx, 4))
+    if variant == "lm":
+        e[:, 1:] = so._lm_F()[1]
+    elif variant == "rlm":
+        e[:, 1:] = so._rlm_F()[1]
+    return e
+
+
+def _oracle_residual(so, variant, x):
+    b = so.rhs(variant)
+    r = so.K(variant, x + _offset(so, variant)) - b
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("variant", ["std", "lm", "rlm"])
+def test_small_fp64_case_to_stagnation(variant):
+    from paper_1907_01027_gb300 import Context
+    p = config1()
+    ref = SweepOracle(p).solve(variant, tol=1e-14, direct=variant != "std")
+    ctx = Context(p, variant, tol=1e-15, max_iters=600)
+    _, phi, st, rc = ctx.solve(allow_stall=True)
+    assert st["resid"] <= 1e-13 * st["resid0"], (rc, st)
+    bound = 1e-12 if variant == "std" else 3e-11
+    assert rel(phi, ref["phi"]) <= bound, st
+    psi = ctx.get_psi()
+    assert rel(psi, ref["psi"] if variant == "std" else ref["psi0"]) <= bound
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", ["std", "lm"])
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4])
+def test_diffusion_limit_sweep_certified_by_oracle(variant, eps):
+    from paper_1907_01027_gb300 import Context
+    p = config2(eps=eps)
+    ctx = Context(p, variant, precond=2, tol=1e-8, max_iters=3000)
+    x, phi, st, rc = ctx.solve()
+    ctx.close()
+    assert rc == 0, st
+    so = SweepOracle(p)
+    # the oracle's residual agrees with the GPU's own to the operators' 1e-12 agreement, relative to |b|
+    assert _oracle_residual(so, variant, x) <= 1.5e-8, st
+
+
+@pytest.fixture(scope="module")
+def blocks():
+    p = config3()
+    return p, SweepOracle(p)
+
+
+def test_blocks_rlm_operator_apply(blocks):
+    from paper_1907_01027_gb300 import Context
+    p, so = blocks
+    ctx = Context(p, "rlm")
+    x = np.random.default_rng(12).standard_normal((p.nx, 4))
+    assert rel(ctx.sweep(x), so.K("rlm", x)) < 1e-12
+    ctx.close()
+
+
+def test_blocks_rlm_solves_certified_by_oracle(blocks):
+    from paper_1907_01027_gb300 import Context
+    p, so = blocks
+    c64 = Context(p, "rlm", tol=1e-10, max_iters=5000)
+    x, phi, st, rc = c64.solve()
+    c64.close()
+    assert rc == 0, st
+    assert _oracle_residual(so, "rlm", x) <= 2e-10, st
+    # the mixed-precision solve (FP32 sweeps, float-float residuals) to 1e-10: its solution leaves the FP64
+    # operator's residual within the tolerance (the two solutions themselves differ by up to kappa 1e-10, and
+    # kappa is large here: pure scatterer against sigma_a = 10 blocks)
+    from paper_1907_01027_gb300 import SWEEP_SOURCE
+    c32 = Context(p, "rlm", tol=1e-10, precision=1, max_iters=5000)
+    x32, _, st32, rc32 = c32.solve(exact_ref=True)
+    c32.close()
+    assert rc32 == 0 and st32["resid"] <= 1e-10 * st32["resid0"], st32
+    c64 = Context(p, "rlm")
+    r = c64.sweep(x32, flags=SWEEP_SOURCE)
+    b = c64.sweep(np.zeros_like(x32), flags=SWEEP_SOURCE)
+    c64.close()
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b), st32

@@ -74,10 +74,17 @@ def test_mixed_solve_with_f32x2_residuals(variant, n, N, eps, seed):
     p = random_problem(n, N, eps, seed)
     ref = SweepOracle(p).solve(variant, direct=True)
     ctx = Context(p, variant, precision=FP32, resid=RESID_F32X2, tol=1e-12, max_iters=20000)
-    _, phi, st, rc = ctx.solve()
+    _, phi, st, rc = ctx.solve(exact_ref=True)
     assert rc == 0, st
     assert st["sweeps_fp64"] == 0 and st["sweeps_f32x2"] >= 1
     assert st["resid"] <= 1e-12 * st["resid0"]
+    # with LMDG_SOLVE_EXACT_REF the tolerance reference ||b|| comes from a float-float sweep; without it, from an
+    # FP32 sweep, within the FP32 sweep's error of the exact norm
+    from paper_1907_01027_gb300 import SWEEP_SOURCE
+    bn = np.linalg.norm(ctx.sweep(np.zeros((p.nx, 4)), flags=SWEEP_SOURCE))
+    assert abs(st["resid0"] - bn) <= 1e-12 * bn, (st["resid0"], bn)
+    _, _, st32, rc32 = ctx.solve()
+    assert rc32 == 0 and abs(st32["resid0"] - bn) <= 1e-5 * bn, (st32["resid0"], bn)
     # kappa * tol: the reduced operators at these sizes have kappa of order 1 / h^2 ~ 1e3
     assert rel(phi, ref["phi"]) < 1e-8
     ctx.close()
