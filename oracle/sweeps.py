@@ -467,7 +467,9 @@ class SweepOracle:
         adds the diffusion correction of the cell averages (:mod:`oracle.dsa`) to it (to the identity for the
         standard scheme and P0-DG), solved exactly or (``dsa_cycles``) by that many multigrid V-cycles;
         ``precond='vdsa'`` is the vertex diffusion correction of :mod:`oracle.vdsa` (each scheme's own diffusion
-        limit) after the Jacobi scaling, its solve exact or ``dsa_cycles`` V-cycles (``mg``: multigrid options)."""
+        limit) after the Jacobi scaling, its solve exact or ``dsa_cycles`` V-cycles (``mg``: multigrid options);
+        ``precond='bvdsa'`` the same correction added to the cell-block Jacobi step B^-1 v, B the diagonal blocks of
+        K (:func:`oracle.vdsa.diagonal_blocks`)."""
         if precond is None:
             precond = "none" if variant in ("std", "p0") else "jacobi"
         b = self.rhs(variant).ravel()
@@ -479,12 +481,13 @@ class SweepOracle:
             X = np.linalg.solve(self.dense_K(variant), b)
         else:
             D = np.ones((self.nx, 4))
-            if variant not in ("std", "p0") and precond in ("jacobi", "dsa", "vdsa"):
+            if variant not in ("std", "p0") and precond in ("jacobi", "dsa", "vdsa", "bvdsa"):
                 D[:, 1:] = self.B11mat().diagonal().reshape(self.nx, 3)
-            if precond == "vdsa":
-                from oracle.vdsa import VertexCorrection
+            if precond in ("vdsa", "bvdsa"):
+                from oracle.vdsa import VertexCorrection, diagonal_blocks
+                blocks = diagonal_blocks(self, variant) if precond == "bvdsa" else None
                 Minv = VertexCorrection(self.p, variant, None if variant == "std" else D[:, 1:], cycles=dsa_cycles,
-                                        **(mg or {}))
+                                        blocks=blocks, **(mg or {}))
             elif precond == "dsa":
                 from oracle.dsa import DiffusionCorrection
                 corr = DiffusionCorrection(self.p, cycles=dsa_cycles)
@@ -496,7 +499,7 @@ class SweepOracle:
             op = spla.LinearOperator((n4, n4), matvec=lambda v: self.K(variant, Minv(v)).ravel(),
                                      dtype=np.float64)
             cnt = [0]
-            if x0 is not None and precond in ("dsa", "vdsa"):
+            if x0 is not None and precond in ("dsa", "vdsa", "bvdsa"):
                 raise ValueError("an initial guess is not supported with the diffusion correction")
             y0 = None if x0 is None else x0.ravel() * (1.0 if precond != "jacobi" else D.ravel())
             Y, ierr = spla.gmres(op, b, x0=y0, rtol=tol, atol=0.0, restart=restart, maxiter=maxiter,

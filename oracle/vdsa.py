@@ -26,6 +26,12 @@ the right preconditioner diag(I, diag(B11))^-1 is applied first.
 
 D_a^-1 is a direct sparse solve, or ``cycles`` V-cycles of the geometric multigrid below (the reference the
 device V-cycle is checked against).
+
+In optically thick cells the correction alone loses its effect: the cells are nearly decoupled and scatter
+nearly everything back, so modes that change from cell to cell converge as slowly as the smooth ones (K's
+eigenvalues there fall to about 1 / (sigma_t h)) and no continuous vertex function carries them.  The block
+variant replaces the Jacobi term by the inverse of K's own diagonal blocks (one 4 x 4 block per cell, found by
+probing K), which is K to leading order on those modes: v -> B^-1 v + C(J v).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -196,17 +202,59 @@ def _block_apply(dinv, r, bs):
     return np.einsum("vcd,vd->vc", dinv, r.reshape(-1, bs)).ravel()
 
 
+def block_key(so, variant, k):
+    """What the diagonal block of cell k depends on: the cell's own solve sees its material (sigma_s, sigma_a),
+    and with the upwind reconstruction of RLMDG also which of its faces lie on the boundary -- the distance to each
+    side, up to 2 for the three-cell slopes of RLMDG* -- and which faces are suppressed."""
+    p = so.p
+    key = (float(p.sigma_s[k]), float(p.sigma_a[k]))
+    if variant == "rlm":
+        i, j = k % p.n, k // p.n
+        key += (min(i, 2), min(p.n - 1 - i, 2), min(j, 2), min(p.rows - 1 - j, 2))
+        if so.supp is not None:
+            key += (int(so.supp[k]),)
+    return key
+
+
+def diagonal_blocks(so, variant):
+    """The diagonal blocks of the reduced operator K of ``variant`` (the homogeneous map of ``so.K``): [n_x][4][4],
+    column r of cell k's block the cell-k part of K e_(k, r).  K applied to a vector that lives in one cell reaches
+    that cell only through its own solve (every other cell it reaches lies downwind), so the block is the same for
+    cells with the same ``block_key``; one cell per key is probed with four applications of K."""
+    nx = so.p.nx
+    B = np.zeros((nx, 4, 4))
+    seen = {}
+    for k in range(nx):
+        key = block_key(so, variant, k)
+        if key not in seen:
+            blk = np.zeros((4, 4))
+            for r in range(4):
+                e = np.zeros((nx, 4))
+                e[k, r] = 1.0
+                blk[:, r] = so.K(variant, e)[k]
+            seen[key] = blk
+        B[k] = seen[key]
+    return B
+
+
 class VertexCorrection:
     """The right preconditioner v -> J v + C(J v) on reduced vectors [n_x][4] for a variant, with J the Jacobi
     scaling diag(I, diag(B11))^-1 of the low-memory schemes (``b11diag``: [n_x][3], None for the standard
     scheme) and C the vertex diffusion correction, its solve direct (``cycles=None``) or by that many V-cycles
-    from zero."""
+    from zero.
 
-    def __init__(self, p, variant, b11diag=None, cycles=None, **mg):
+    With ``blocks`` (the diagonal blocks of K, :func:`diagonal_blocks`) the first term is the cell-block Jacobi
+    step instead: v -> B^-1 v + C(J v).  In optically thick cells most of K's slow modes vary from cell to cell
+    (the cells are nearly decoupled and scatter nearly everything back), which no continuous vertex function
+    represents; on these the block of K is K to leading order, and B^-1 takes them to eigenvalues near 1 while
+    C takes the smooth ones."""
+
+    def __init__(self, p, variant, b11diag=None, cycles=None, blocks=None, **mg):
         self.p, self.variant, self.cycles = p, variant, cycles
         self.kind = stiffness_kind(variant)
         self.A = vertex_matrix(p, self.kind)
         self.b11diag = b11diag
+        self.binv = None if blocks is None else np.linalg.inv(blocks)
         if cycles is None:
             self.lu = spla.splu(self.A.tocsc())
         else:
@@ -225,12 +273,15 @@ class VertexCorrection:
         return interpolate(self.p, self.solve(load(self.p, u)))
 
     def __call__(self, v):
-        u = np.array(v, dtype=float).reshape(self.p.nx, 4)
+        v = np.array(v, dtype=float).reshape(self.p.nx, 4)
+        u = v.copy()
         if self.variant != "std":
             u[:, 1:] /= self.b11diag
             phi = u.copy()
             phi[:, 1:] *= -1.0
             c = self.correction(phi)
             c[:, 1:] *= -1.0
-            return (u + c).ravel()
-        return (u + self.correction(u)).ravel()
+        else:
+            c = self.correction(u)
+        first = u if self.binv is None else np.einsum("krs,ks->kr", self.binv, v)
+        return (first + c).ravel()
