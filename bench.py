@@ -444,12 +444,16 @@ def run_gpu(args, rank, ws, dist):
 
 # iteration caps of the eps = 1e-3 solves (GMRES iterations, all refinement steps)
 DIFFUSIVE_MAX_ITERS = {"std": 2000, "lm": 3000, "rlm": 1500}
+# lmdg_options.precond of the eps = 1e-3 solves: 2 (vertex correction) or 3 (with the cell-block step); measured at
+# 1024^2 S16 mixed: Q1-DG 68 / 72 iterations, LMDG 227 / 210, RLMDG 1350 / 1200
+DIFFUSIVE_PRECOND = {"std": 2, "lm": 3, "rlm": 3}
 
 
 def diffusive_times(args, local):
     """Time to 1e-8 at eps = 1e-3 on the 1024^2 S16 patch medium (sigma_t h from 0.1 to 10): per scheme the mixed
     solver (FP32 sweeps, FP64 residual sweeps, FP64 refinement) and the FP64 solver, both with the vertex diffusion
-    correction, one timed solve each after the context's workspace is allocated."""
+    correction (DIFFUSIVE_PRECOND: with the cell-block step for LMDG and RLMDG, which takes fewer iterations there,
+    without it for Q1-DG, which takes more), one timed solve each after the context's workspace is allocated."""
     import numpy as np
     import torch
     from paper_1907_01027_gb300 import Context, FP32, FP64, RESID_FP64
@@ -463,14 +467,16 @@ def diffusive_times(args, local):
         for mode, kw in (("mixed", dict(precision=FP32, resid=RESID_FP64)), ("fp64", dict(precision=FP64))):
             if args.skip_fp64 and mode == "fp64":
                 continue
-            ctx = Context(p, v, precond=2, tol=1e-8, max_iters=DIFFUSIVE_MAX_ITERS[v], device=local, **kw)
+            ctx = Context(p, v, precond=DIFFUSIVE_PRECOND[v], tol=1e-8, max_iters=DIFFUSIVE_MAX_ITERS[v],
+                          device=local, **kw)
             ctx.precond_apply(np.zeros((p.nx, 4)))          # allocates the Krylov workspace outside the timing
             torch.cuda.synchronize()
             e0.record()
             _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
             e1.record()
             torch.cuda.synchronize()
-            res[v][mode] = {"ms": e0.elapsed_time(e1), "status": rc, "iters": st["iters"],
+            res[v][mode] = {"ms": e0.elapsed_time(e1), "status": rc, "precond": DIFFUSIVE_PRECOND[v],
+                            "iters": st["iters"],
                             "refinements": st["refinements"], "resid": st["resid"] / st["resid0"],
                             "sweeps_fp32": st["sweeps_fp32"], "sweeps_fp64": st["sweeps_fp64"],
                             "sweep_ms_fp32": st["sweep_ms_fp32"], "sweep_ms_fp64": st["sweep_ms_fp64"]}

@@ -98,7 +98,8 @@ typedef struct {
   int max_refine;      /* FP32 modes: cap on outer refinement steps (default 50) */
   int precond;         /* right preconditioner of GMRES: 1 (default) diag(I, diag(B11))^-1 for LMDG/RLMDG (the
                           identity for Q1-DG); 0 none; 2 the same followed by the vertex diffusion correction
-                          (lmdg_precond_apply) for the diffusive regime -- not for LMDG_P0 (LMDG_ERR_ARG) */
+                          (lmdg_precond_apply) for the diffusive regime; 3 the correction added to the cell-block
+                          Jacobi step (optically thick cells) -- 2 and 3 not for LMDG_P0 (LMDG_ERR_ARG) */
   long long spin_limit;/* polls of a readiness flag before a sweep reports LMDG_ERR_TIMEOUT (default 2^26) */
   int device;          /* CUDA device ordinal (default 0) */
   int suppress;        /* LMDG_RLM only, 1: no reconstruction across an interior face where sigma_s or sigma_a
@@ -235,8 +236,12 @@ int lmdg_b11_solve(lmdg_ctx *ctx, const double *r, double *z, double tol, int *i
  * prolongation, two components per coarse vertex below the finest level of the cell-average operator, Galerkin
  * coarse operators, two damped block-Jacobi steps (omega = 0.7) before and after, dense coarsest solve up to
  * 1156 unknowns, else 50 Jacobi steps; levels halve nx and ny while both are even and above 2), built by
- * lmdg_setup.  x and y distinct; asynchronous on stream for
- * device pointers. */
+ * lmdg_setup.  precond 3: y = B^-1 x + C(J x), C the correction above, J the scaling of precond 1 and B the
+ * cell-diagonal blocks of K (one 4 x 4 block per cell: the part of K e_(K,r) in cell K, found by lmdg_setup with
+ * four FP64 sweeps in which no cell sees upwind data, and inverted per cell; LMDG_ERR_BREAKDOWN from lmdg_setup if
+ * a block has no usable pivot).  In optically thick cells most slow modes of the iteration change from cell to
+ * cell and no vertex function carries them; on these K acts through its diagonal blocks to leading order.
+ * x and y distinct; asynchronous on stream for device pointers. */
 int lmdg_precond_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, void *stream);
 
 /* Operator application that allocates nothing (no counterpart in the paper: it is a deployment variant of

@@ -133,6 +133,7 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   }
   if constexpr (P == 0) a.corr = c->corr;
   a.supp = c->supp;
+  if constexpr (P == 0) a.local = c->local_mode;
   a.coef = nullptr; a.ncoef = 0; a.ncls = 0; a.cls = nullptr; a.matsh = nullptr; a.mat = nullptr;
   // coefficient tables for the FP64 and float-float sweeps, where they replace reciprocals and Schur products;
   // the FP32 sweeps form the coefficients with the hardware reciprocal as fast as they would load them
@@ -357,13 +358,16 @@ cudaError_t to_float(const double *x, float *y, size_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// y = Minv x: the right preconditioner of GMRES -- diag(I, diag(B11))^-1 for the low-memory schemes (precond >= 1),
-// then with precond = 2 the vertex diffusion correction y += I_h D_a^-1 R_h (sigma_s/eps) y (one V-cycle)
+// y = Minv x: the right preconditioner of GMRES -- J = diag(I, diag(B11))^-1 for the low-memory schemes
+// (precond >= 1), then with precond = 2 the vertex diffusion correction y += I_h D_a^-1 R_h (sigma_s/eps) y (one
+// V-cycle); precond = 3 replaces the J x term by the cell-block Jacobi step: y = B^-1 x + C(J x), B the diagonal
+// blocks of K
 int apply_minv(lmdg_ctx *c, double *y, const double *x, cudaStream_t s) {
   const bool lowmem = c->variant == LMDG_LM || c->variant == LMDG_RLM;
   const int pmode = (lowmem && c->opt.precond) ? 1 : 0;
   CK(precond(y, x, c->b11dinv, c->nx, pmode, s));
-  if (c->opt.precond == 2) CK(dsa_apply(c->dsa, c->ni, c->nj, c->h, c->d64.sse, lowmem ? 1 : 0, y, s));
+  if (c->opt.precond >= 2) CK(dsa_apply(c->dsa, c->ni, c->nj, c->h, c->d64.sse, lowmem ? 1 : 0, y, s));
+  if (c->opt.precond == 3) CK(block_step(y, x, c->binv, c->b11dinv, c->nx, pmode, s));
   return 0;
 }
 
@@ -507,7 +511,7 @@ void lmdg_destroy(lmdg_ctx *c) {
   lmdg::dfree(c->p1ra2); lmdg::dfree(c->coef2); lmdg::dfree(c->qadj2);
   lmdg::dfree(c->perm); lmdg::dfree(c->p1ra64); lmdg::dfree(c->p1ra32); lmdg::dfree(c->sq1); lmdg::dfree(c->b11dinv);
   lmdg::dfree(c->sigma_a); lmdg::dfree(c->qmom); lmdg::dfree(c->part); lmdg::dfree(c->ytr); lmdg::dfree(c->ctrl);
-  lmdg::dfree(c->psi);
+  lmdg::dfree(c->psi); lmdg::dfree(c->binv);
   lmdg::dfree(c->cellsrc); lmdg::dfree(c->cellsh);
   lmdg::dfree(c->rev); lmdg::dfree(c->qadj64); lmdg::dfree(c->qadj32); lmdg::dfree(c->adj_buf);
   lmdg::dfree(c->mat); lmdg::dfree(c->cls); lmdg::dfree(c->matsh); lmdg::dfree(c->coef); lmdg::dfree(c->supp);
@@ -572,8 +576,8 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (o.restart < 1 || o.restart > 120 || o.max_iters < 1 || !(o.tol > 0) || o.spin_limit < 1 ||
       (o.suppress != 0 && o.suppress != 1) || (o.suppress && variant != LMDG_RLM) || o.recon < 0 || o.recon > 2 ||
       (o.recon && (variant != LMDG_RLM || o.suppress)) ||
-      (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2) || o.precond < 0 || o.precond > 2 ||
-      (o.precond == 2 && variant == LMDG_P0))
+      (o.resid != LMDG_RESID_FP64 && o.resid != LMDG_RESID_F32X2) || o.precond < 0 || o.precond > 3 ||
+      (o.precond >= 2 && variant == LMDG_P0))
     return LMDG_ERR_ARG;
   phase("validation");
   int ndev = 0;
@@ -848,7 +852,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     }
   }
   phase("coefficient tables");
-  if (o.precond == 2) {
+  if (o.precond >= 2) {
     // vertex diffusion correction of the scheme's own diffusion limit (full gradient for Q1-DG, cell-averaged
     // gradient for the low-memory schemes), multigrid hierarchy built on the device
     if (int e2 = dsa_build(c->dsa, variant == LMDG_STD ? 0 : 1, ni, nj, h, eps, c->d64.sigt, c->sigma_a, Ax[0], Ay[0],
@@ -856,6 +860,32 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
       return fail(e2);
   }
   phase("diffusion correction");
+  if (o.precond == 3) {
+    // the cell-diagonal blocks of K: four FP64 sweeps with the upwind coupling cut, of x = e_r in every cell
+    // (column r of every block), then one 4 x 4 inverse per cell
+    if (lmdg::dmalloc(&c->binv, sizeof(double) * 16 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+    double *tmp = nullptr;   // x = e_r, then the four columns
+    if (lmdg::dmalloc(&tmp, sizeof(double) * 20 * nx) != cudaSuccess) return fail(LMDG_ERR_NOMEM);
+    double *ycol = tmp + 4 * (size_t)nx;
+    c->local_mode = 1;
+    int e2 = 0;
+    for (int r = 0; r < 4 && !e2; ++r) {
+      if (unit_vectors(tmp, nx, r, nullptr) != cudaSuccess) e2 = LMDG_ERR_CUDA;
+      else e2 = do_sweep<double>(c, tmp, ycol + 4 * (size_t)nx * r, 0, false, 0, nullptr);
+    }
+    c->local_mode = 0;
+    if (!e2) e2 = check_error_word(c, nullptr);
+    unsigned *bad = c->ctrl + 2;
+    unsigned nbad = 0;
+    if (!e2 && (block_inverses(ycol, ycol + 4 * (size_t)nx, ycol + 8 * (size_t)nx, ycol + 12 * (size_t)nx, nx,
+                               c->binv, bad, nullptr) != cudaSuccess ||
+                cudaMemcpy(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess))
+      e2 = LMDG_ERR_CUDA;
+    lmdg::dfree(tmp);
+    if (!e2 && nbad) e2 = LMDG_ERR_BREAKDOWN;
+    if (e2) return fail(e2);
+  }
+  phase("cell blocks");
   *out = c;
   return 0;
 }

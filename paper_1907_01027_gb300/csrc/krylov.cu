@@ -295,6 +295,84 @@ cudaError_t axpby(double *y, double a, const double *x, double b, size_t N, cuda
   axpby_kernel<<<grid_for(N), 256, 0, s>>>(y, a, x, b, N);
   return cudaGetLastError();
 }
+__global__ void unit_kernel(double *__restrict__ x, int nx, int r) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  for (int q = 0; q < 4; ++q) x[4 * (size_t)K + q] = q == r ? 1.0 : 0.0;
+}
+
+// One 4 x 4 inverse per cell by Gauss-Jordan elimination on [B | I] with partial pivoting.
+__global__ void block_inverse_kernel(const double *__restrict__ y0, const double *__restrict__ y1,
+                                     const double *__restrict__ y2, const double *__restrict__ y3, int nx,
+                                     double *__restrict__ binv, unsigned *__restrict__ bad) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double *col[4] = {y0, y1, y2, y3};
+  double a[4][8];
+  double scale = 0;
+  for (int q = 0; q < 4; ++q)
+    for (int r = 0; r < 4; ++r) {
+      a[q][r] = col[r][4 * (size_t)K + q];
+      a[q][4 + r] = q == r ? 1.0 : 0.0;
+      scale = fmax(scale, fabs(a[q][r]));
+    }
+  bool ok = scale > 0 && isfinite(scale);
+  for (int c = 0; c < 4 && ok; ++c) {
+    int piv = c;
+    for (int q = c + 1; q < 4; ++q)
+      if (fabs(a[q][c]) > fabs(a[piv][c])) piv = q;
+    if (!(fabs(a[piv][c]) > 1e-14 * scale)) { ok = false; break; }
+    if (piv != c)
+      for (int r = 0; r < 8; ++r) { const double t = a[c][r]; a[c][r] = a[piv][r]; a[piv][r] = t; }
+    const double inv = 1.0 / a[c][c];
+    for (int r = 0; r < 8; ++r) a[c][r] *= inv;
+    for (int q = 0; q < 4; ++q) {
+      if (q == c) continue;
+      const double f = a[q][c];
+      if (f != 0.0)
+        for (int r = 0; r < 8; ++r) a[q][r] -= f * a[c][r];
+    }
+  }
+  double *o = binv + 16 * (size_t)K;
+  for (int q = 0; q < 4; ++q)
+    for (int r = 0; r < 4; ++r) o[4 * q + r] = ok ? a[q][4 + r] : (q == r ? 1.0 : 0.0);
+  if (!ok) atomicAdd(bad, 1u);
+}
+
+__global__ void block_step_kernel(double *__restrict__ y, const double *__restrict__ x,
+                                  const double *__restrict__ binv, const double *__restrict__ dinv, int nx, int mode) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nx) return;
+  const double *xk = x + 4 * (size_t)K;
+  const double *b = binv + 16 * (size_t)K;
+  double *yk = y + 4 * (size_t)K;
+  for (int q = 0; q < 4; ++q) {
+    const double jx = (mode == 1 && q > 0) ? xk[q] * dinv[3 * (size_t)K + q - 1] : xk[q];
+    const double bx = b[4 * q] * xk[0] + b[4 * q + 1] * xk[1] + b[4 * q + 2] * xk[2] + b[4 * q + 3] * xk[3];
+    yk[q] += bx - jx;
+  }
+}
+
+cudaError_t unit_vectors(double *x, int nx, int r, cudaStream_t s) {
+  add_launches(1);
+  unit_kernel<<<(nx + 255) / 256, 256, 0, s>>>(x, nx, r);
+  return cudaGetLastError();
+}
+cudaError_t block_inverses(const double *y0, const double *y1, const double *y2, const double *y3, int nx,
+                           double *binv, unsigned *bad, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  add_launches(1);
+  block_inverse_kernel<<<(nx + 127) / 128, 128, 0, s>>>(y0, y1, y2, y3, nx, binv, bad);
+  return cudaGetLastError();
+}
+cudaError_t block_step(double *y, const double *x, const double *binv, const double *dinv, int nx, int mode,
+                       cudaStream_t s) {
+  add_launches(1);
+  block_step_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, binv, dinv, nx, mode);
+  return cudaGetLastError();
+}
+
 cudaError_t precond(double *y, const double *x, const double *dinv, int nx, int mode, cudaStream_t s) {
   add_launches(1);
   precond_kernel<<<(nx + 255) / 256, 256, 0, s>>>(y, x, dinv, nx, mode);

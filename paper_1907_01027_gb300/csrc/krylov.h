@@ -23,6 +23,16 @@ cudaError_t b11_apply(int ni, int nj, double h, double eps, const double *sigma_
 // reduced solutions (standard) or scalar-flux moments (low-memory)
 cudaError_t adjoint_gradients(int variant, int nx, int P, double h, double eps, const double *part,
                               const double *Phi, const double *Lam, double *out, cudaStream_t s);
+// x[4K + q] = (q == r) for every cell K < nx: one unit Legendre moment in every cell
+cudaError_t unit_vectors(double *x, int nx, int r, cudaStream_t s);
+// binv[K] = B_K^-1 with B_K[q][r] = y_r[4K + q] (Gauss-Jordan elimination with partial pivoting, FP64); cells
+// whose block has no usable pivot add 1 to *bad (zeroed here first) and get the identity
+cudaError_t block_inverses(const double *y0, const double *y1, const double *y2, const double *y3, int nx,
+                           double *binv, unsigned *bad, cudaStream_t s);
+// y += binv x - J x per cell, J = diag(I, 1/dinv)^-1 (mode 1) or the identity (mode 0): turns J x + C(J x) into the
+// cell-block step B^-1 x + C(J x)
+cudaError_t block_step(double *y, const double *x, const double *binv, const double *dinv, int nx, int mode,
+                       cudaStream_t s);
 // p[0..N) = v
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s);
 // stored psi (column-major per direction, kind 0 double, 1 float, 2 bfloat16; per values per cell) to the user

@@ -79,6 +79,9 @@ struct SweepArgs {
   const double *matsh; // [materials] sigma_t h of each material
   const int *mat;      // [nx] material of each cell (prep_kernel writes it into the cellsh slot)
   const unsigned *supp;  // RLMDG: [nx] faces without reconstruction (1 west, 2 east, 4 south, 8 north) or null
+  int local;           // FP64 only: every cell's solve sees zero upwind data (the traces from its left and lower
+                       // neighbours, the slope traces of LMDG, the upwind values of the reconstruction), so that
+                       // y = K x returns the cell-diagonal blocks of K applied to x
 };
 
 // Vertex diffusion correction (dsa.cu): one multigrid level, nine-point stencils of bs x bs blocks on the
@@ -222,5 +225,7 @@ struct lmdg_ctx {
   double *coef = nullptr;                  // [nmat][ncls][ncoef]
   lmdg::f2 *coef2 = nullptr;               // the same, float-float
   unsigned *supp = nullptr;                // RLMDG suppression bits per cell, or null
-  lmdg::VertexDsa dsa;                     // vertex diffusion correction (precond = 2)
+  lmdg::VertexDsa dsa;                     // vertex diffusion correction (precond = 2, 3)
+  double *binv = nullptr;                  // precond = 3: [nx][4][4] inverses of K's cell-diagonal blocks
+  int local_mode = 0;                      // FP64 sweeps cut the upwind coupling (SweepArgs::local)
 };

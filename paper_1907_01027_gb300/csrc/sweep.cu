@@ -403,6 +403,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   // the adjoint correlation exists for the FP64 instances only (compiled out of FP32)
   constexpr bool kF64 = std::is_same<T, double>::value;
   const bool use_corr = kF64 && !LEAN && A.corr != nullptr;
+  const bool local = kF64 && !LEAN && A.local != 0;   // cut the upwind coupling (diagonal blocks of K)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit, s_abort;
 
@@ -634,6 +635,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         if (VAR == 1) {
           yl1_in = shfl_up1(yl1);
           if (lane == 0) yl1_in = (ybnd || nA == 0) ? (T)0 : yws[1];
+          if (local) { yl1_in = 0; xl1 = 0; }
         }
         const T A13 = A1 + A3, A23 = A2 + A3;
 
@@ -649,6 +651,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
               if (lane == 0) {
 #pragma unroll
                 for (int c = 0; c < NSH; ++c) yin[c] = ybnd ? (T)0 : yws[(size_t)k * C * NS + c];
+              }
+              if (local) {
+#pragma unroll
+                for (int c = 0; c < NS; ++c) { yin[c] = 0; xs[k][c] = 0; }
               }
               const T a = aA[k], bb = bA[k], wl = wA[k];
               // inflow boundary data (source sweeps): left face on x == 0, bottom face on the first row

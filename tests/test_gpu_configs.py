@@ -6,8 +6,9 @@
   number kappa differ by up to about kappa times the rounding of the operator (a few 1e-16): 1e-12 for Q1-DG, and
   3e-11 for LMDG and RLMDG, whose reduced operators have kappa = 1.3e4 and 1.4e4 here.
 * 256^2 cells, S8, sigma_s = sigma_a = 1, eps in {1, 1e-2, 1e-4} (the diffusion-limit sweep): Q1-DG and LMDG
-  solves with the vertex diffusion correction to 1e-8, each certified by the oracle: the oracle's reduced
-  operator applied to the GPU's solution leaves a residual within the solve's tolerance.  (At eps = 1e-4 the
+  solves with the vertex diffusion correction and the cell-block step (precond = 3) to 1e-8, each certified by
+  the oracle: the oracle's reduced operator applied to the GPU's solution leaves a residual within the solve's
+  tolerance.  (At eps = 1e-4 the
   reduced operator's smallest eigenvalues are of order eps^2, and the FP64 residual of an exact solution is
   itself near 1e-9 of |b|: 1e-8 is the tolerance FP64 reaches there.)
 * 512^2 cells, S12, the 7x7 block pattern of absorbing blocks (sigma_s = 0, sigma_a = 10) in a pure scatterer,
@@ -64,7 +65,7 @@ def test_small_fp64_case_to_stagnation(variant):
 def test_diffusion_limit_sweep_certified_by_oracle(variant, eps):
     from paper_1907_01027_gb300 import Context
     p = config2(eps=eps)
-    ctx = Context(p, variant, precond=2, tol=1e-8, max_iters=3000)
+    ctx = Context(p, variant, precond=3, tol=1e-8, max_iters=3000)
     x, phi, st, rc = ctx.solve()
     ctx.close()
     assert rc == 0, st
