@@ -176,10 +176,12 @@ class Context:
         self._check(rc, "lmdg_sweep")
         return y
 
-    def solve(self, x0=None, want_x=True, want_phi=True, device=False, allow_stall=False, exact_ref=False):
+    def solve(self, x0=None, want_x=True, want_phi=True, device=False, allow_stall=False, exact_ref=False,
+              phi_out=None):
         """lmdg_solve.  Returns (x, phi, stats dict, status).  LMDG_ERR_NOTCONV returns normally (outputs written);
         with ``allow_stall`` so does LMDG_ERR_BREAKDOWN from a residual that stopped decreasing (a solve driven
-        below what the arithmetic can reach).  ``exact_ref``: LMDG_SOLVE_EXACT_REF."""
+        below what the arithmetic can reach).  ``exact_ref``: LMDG_SOLVE_EXACT_REF.  ``phi_out``: a host array
+        [N][4] of float64 (pinned memory, for instance) that receives phi instead of a new one."""
         st = Stats()
         fl = SOLVE_EXACT_REF if exact_ref else 0
         if device:
@@ -191,7 +193,12 @@ class Context:
                                      ctypes.byref(st), fl, _stream())
         else:
             x = np.empty((self.nx, 4)) if want_x else None
-            phi = np.empty((self.nx, 4)) if want_phi else None
+            if phi_out is not None:
+                if phi_out.dtype != np.float64 or phi_out.shape != (self.nx, 4) or not phi_out.flags.c_contiguous:
+                    raise ValueError("phi_out must be a C-contiguous float64 array of shape (N, 4)")
+                phi = phi_out
+            else:
+                phi = np.empty((self.nx, 4)) if want_phi else None
             x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
             rc = self.lib.lmdg_solve(self.h, None if x0a is None else x0a.ctypes.data,
                                      None if x is None else x.ctypes.data, None if phi is None else phi.ctypes.data,

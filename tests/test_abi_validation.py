@@ -124,14 +124,14 @@ def test_resid_option_validated(L):
 
 
 def test_precond_option_validated(L):
-    """The preconditioner takes 0, 1 or 2 (the vertex diffusion correction), and 2 is refused for P0-DG, whose
-    scheme has no diffusion limit."""
+    """The preconditioner takes 0, 1, 2 (the vertex diffusion correction) or 3 (with the cell-block step), and 2
+    and 3 are refused for P0-DG, whose scheme has no diffusion limit."""
     from paper_1907_01027_gb300.lmdg import Mesh, Quad, Options
     p = uniform_problem(4, 4, 1.0, 1.0, 1.0)
     mesh = Mesh(p.n, p.rows, p.x0, p.y0, p.h)
     arrs = [np.ascontiguousarray(a) for a in (p.ox, p.oy, p.w, p.sigma_s, p.sigma_a, p.q)]
     quad = Quad(len(p.w), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
-    for variant, pc in ((0, -1), (1, 3), (3, 2)):
+    for variant, pc in ((0, -1), (1, 4), (3, 2), (3, 3)):
         o = Options()
         L.lmdg_default_options(ctypes.byref(o))
         assert o.precond == 1
