@@ -565,8 +565,10 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
   if (std::fabs(wsum - 1.0) > 1e-12) return LMDG_ERR_QUAD;
   if (cnt[0] != na / 4 || cnt[1] != na / 4 || cnt[2] != na / 4 || cnt[3] != na / 4) return LMDG_ERR_QUAD;
   const size_t nx = (size_t)ni * nj;
+  // a cell with the cross sections of the cell before it (piecewise-constant media) passed the same test
   for (size_t K = 0; K < nx; ++K) {
     const double ss = sigma_s[K], sa = sigma_a[K];
+    if (K > 0 && ss == sigma_s[K - 1] && sa == sigma_a[K - 1]) continue;
     if (!(ss >= 0) || !(sa >= 0) || !std::isfinite(ss) || !std::isfinite(sa) || !(ss / eps + eps * sa > 0))
       return LMDG_ERR_ARG;
   }
@@ -809,6 +811,7 @@ int lmdg_setup(lmdg_ctx **out, const lmdg_mesh *mesh, const lmdg_quadrature *qua
     std::vector<double> uniq;
     double prev = 0.0;
     for (size_t K = 0; K < nx; ++K) {
+      if (K > 0 && sigma_s[K] == sigma_s[K - 1] && sigma_a[K] == sigma_a[K - 1]) continue;   // same sigma_t h
       const double shK = (sigma_s[K] / eps + eps * sigma_a[K]) * h;
       if (K == 0 || shK != prev) uniq.push_back(shK);
       prev = shK;

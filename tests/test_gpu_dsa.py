@@ -108,18 +108,27 @@ def test_mixed_precision_diffusive(variant):
 
 @pytest.mark.parametrize("variant,n,eps,kw", [("std", 16, 1e-3, {}), ("lm", 16, 1e-3, {}), ("rlm", 16, 1e-3, {}),
                                               ("std", 37, 1e-2, {}), ("lm", 37, 1e-2, {}),
-                                              ("rlm", 12, 1e-3, {"suppress": 1})])
+                                              ("rlm", 12, 1e-3, {"suppress": 1}), ("std", (24, 13), 1e-3, {}),
+                                              ("rlm", (13, 24), 1e-2, {})])
 def test_block_precond_apply_matches_oracle(variant, n, eps, kw):
     """y = B^-1 x + C(J x) on the device (blocks from the FP64 sweeps without upwind coupling) against the
-    oracle's (blocks by probing its reduced operator, one V-cycle)."""
+    oracle's (blocks by probing its reduced operator, one V-cycle); square and rectangular meshes (the first rows
+    of the square medium)."""
     from oracle.vdsa import diagonal_blocks
-    p = _medium(n, eps)
+    if isinstance(n, tuple):
+        p = _medium(n[0], eps)
+        ny = n[1]
+        p.ny = ny
+        p.sigma_s, p.sigma_a, p.q = p.sigma_s[:n[0] * ny].copy(), p.sigma_a[:n[0] * ny].copy(), p.q[:n[0] * ny].copy()
+        n = n[0]
+    else:
+        p = _medium(n, eps)
     so = SweepOracle(p, suppress=bool(kw.get("suppress")))
     b11 = None if variant == "std" else so.B11mat().diagonal().reshape(p.nx, 3)
     ref = VertexCorrection(p, variant, b11, cycles=1, blocks=diagonal_blocks(so, variant))
     from paper_1907_01027_gb300 import Context
     ctx = Context(p, variant, precond=3, **kw)
-    rng = np.random.default_rng(n + 3)
+    rng = np.random.default_rng(p.nx + 3)
     for _ in range(2):
         x = rng.standard_normal((p.nx, 4))
         assert rel(ctx.precond_apply(x), ref(x).reshape(p.nx, 4)) < 1e-12
