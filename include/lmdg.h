@@ -25,6 +25,8 @@
 #ifndef LMDG_H
 #define LMDG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -73,7 +75,8 @@ enum {
   LMDG_ERR_TIMEOUT = -6,    /* a sweep kernel gave up waiting for an upstream tile (spin limit); the
                                kernel exits cleanly and the context stays usable */
   LMDG_ERR_BREAKDOWN = -7,  /* non-finite residual or Krylov breakdown */
-  LMDG_ERR_STATE = -8       /* call out of order (e.g. lmdg_get_psi before a storing sweep) */
+  LMDG_ERR_STATE = -8,      /* call out of order (e.g. lmdg_get_psi before a storing sweep) */
+  LMDG_ERR_EXCHANGE = -9    /* the exchange callback of a sharded context (lmdg_set_shard) returned nonzero */
 };
 
 typedef struct {
@@ -266,6 +269,49 @@ int lmdg_precond_apply(lmdg_ctx *ctx, const double *x, double *y, int flags, voi
 int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, const double *ox, const double *oy,
                        const double *w, const double *sigma_t, const double *sigma_s_over_eps,
                        const double *x, double *y, long long spin_limit, void *stream);
+
+/* ---- Angle sharding (Section 2.1.1: L is block diagonal over the directions, so every direction's sweep is
+ * independent and only the angular reduction couples them).  A sweep's reduction is formed from "partial sets":
+ * one per (quadrant, direction group) of the launch shape, each an [N][NR] array (NR reduced values per cell) in
+ * the sweep's arithmetic (double; float for LMDG_SWEEP_FP32; a pair of floats, 8 bytes, for LMDG_SWEEP_F32X2),
+ * summed by the epilogue in a fixed order.  Sharding splits the sets into nshards contiguous chunks of chunk_sets
+ * sets; shard r sweeps the directions of chunk r over the whole mesh, and once every chunk is in place the
+ * epilogue gives a result bitwise equal to the unsharded sweep.  A partial buffer holds nshards * chunk_sets sets
+ * (chunk r at byte offset r * chunk_bytes; sets past the last one are padding).  Contexts of one problem set up
+ * with the same arguments (and the same LMDG_SWEEP_GEOM environment) have the same layout. */
+
+/* Layout of the partial sets for the arithmetic of flags (LMDG_SWEEP_FP32 / LMDG_SWEEP_F32X2 / neither) split
+ * into nshards chunks (1 <= nshards <= 4096): the number of sets, the sets per chunk and the bytes per chunk (any
+ * pointer may be NULL). */
+int lmdg_shard_layout(const lmdg_ctx *ctx, int flags, int nshards, int *sets, int *chunk_sets, size_t *chunk_bytes);
+
+/* Sweep the directions of chunk `shard` of nshards at x (DEVICE [N][4]) and write their partial sets into chunk
+ * `shard` of parts (DEVICE, nshards * chunk_bytes bytes, 16-byte aligned; the other chunks are not touched).
+ * flags: LMDG_SWEEP_SOURCE, LMDG_SWEEP_FP32 or LMDG_SWEEP_F32X2, LMDG_SWEEP_STORE (this shard's directions only);
+ * LMDG_HOST_PTRS returns LMDG_ERR_ARG.  Synchronises the stream (reads the sweep's error word). */
+int lmdg_sweep_shard(lmdg_ctx *ctx, const double *x, void *parts, int shard, int nshards, int flags,
+                     void *stream);
+
+/* The epilogue of lmdg_sweep from a complete partial buffer (every chunk written by lmdg_sweep_shard, here or on
+ * other GPUs): y = K x, or K x - b with LMDG_SWEEP_SOURCE, as lmdg_sweep gives for the same flags; x, parts, y
+ * DEVICE pointers.  Asynchronous on stream. */
+int lmdg_sweep_combine(lmdg_ctx *ctx, const double *x, const void *parts, double *y, int flags, void *stream);
+
+/* Exchange callback of a sharded context: on entry chunk `shard` of parts (nshards chunks of chunk_bytes, DEVICE,
+ * in the arithmetic of flags) holds this shard's partial sets, written on stream; on return every other chunk
+ * must be filled, or be filled by work ordered on stream -- an all-gather in place over the shards' GPUs (for
+ * instance NCCL's).  x is the sweep's input and flags its lmdg_sweep flags (for callers that sweep the other
+ * chunks themselves).  Return 0, or nonzero to fail the sweep with LMDG_ERR_EXCHANGE. */
+typedef int (*lmdg_exchange_fn)(void *user, void *parts, size_t chunk_bytes, int nshards, const double *x,
+                                int flags, void *stream);
+
+/* Make every later sweep of the context (lmdg_sweep, and every sweep of lmdg_solve including its recovery sweep)
+ * sweep chunk `shard` of nshards only and call fn(user, ...) before its epilogue; nshards = 1 undoes it (fn may
+ * then be NULL).  GMRES vectors stay replicated: every shard runs the same solve, and with identical
+ * inputs gets identical iterates.  Stored angular unknowns are sharded by direction: lmdg_get_psi returns this
+ * shard's directions, the other directions' entries are undefined.  lmdg_adjoint on a sharded context returns
+ * LMDG_ERR_STATE (its correlation sweep reads the opposite directions' stored unknowns). */
+int lmdg_set_shard(lmdg_ctx *ctx, int shard, int nshards, lmdg_exchange_fn fn, void *user);
 
 /* Problem sizes of a context: cells along x and y, n_Omega, variant (any pointer may be NULL). */
 int lmdg_info(const lmdg_ctx *ctx, int *nx, int *ny, int *n_omega, int *variant);

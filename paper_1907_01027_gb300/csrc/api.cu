@@ -85,8 +85,31 @@ int ensure_f2(lmdg_ctx *c, cudaStream_t s) {
   return 0;
 }
 
+// Angle sharding: the 4 * groups partial sets of a launch shape are split into nshards contiguous chunks of
+// ceil(4 * groups / nshards) sets; shard r sweeps the directions of chunk r (empty for r beyond the sets).
+struct ShardRange { int sets, chunk, pq0, npq; };
+ShardRange shard_range(const SweepGeom &g, int shard, int nshards) {
+  ShardRange r{};
+  r.sets = 4 * g.groups;
+  r.chunk = (r.sets + nshards - 1) / nshards;
+  r.pq0 = std::min(r.sets, shard * r.chunk);
+  r.npq = std::min(r.sets, (shard + 1) * r.chunk) - r.pq0;
+  return r;
+}
+
+// lmdg_sweep flags of an internal sweep (what the exchange callback is told)
+int sweep_flags(int prec, int source, bool store) {
+  return (source ? LMDG_SWEEP_SOURCE : 0) | (prec == 1 ? LMDG_SWEEP_FP32 : 0) | (prec == 2 ? LMDG_SWEEP_F32X2 : 0) |
+         (store ? LMDG_SWEEP_STORE : 0);
+}
+
+// One transport sweep with its angular reduction.  mode 0: sweep and epilogue (y = K x or K x - b); a context
+// sharded by lmdg_set_shard sweeps its own chunk of partial sets and calls the exchange callback before the
+// epilogue.  mode 1: sweep the partial sets of (shard, nshards) into ext (the full [chunks * chunk][nx][NR] layout,
+// only this shard's chunk written), no epilogue.  mode 2: epilogue only, from the partial sets in ext.
 template <typename T>
-int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s) {
+int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s,
+             int mode = 0, int shard = 0, int nshards = 1, void *ext = nullptr) {
   SweepArgs<T> a{};
   constexpr int P = prec_of<T>();
   const bool f64 = P == 0;
@@ -103,9 +126,15 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.q_per_angle = c->q_layout == 2;
   a.X = X;
   a.source = source;
-  {
-    // partial reductions of this launch shape and arithmetic: the buffer grows to the largest one used
-    const size_t pbytes = (size_t)4 * a.g.groups * c->nx * nr_of(c->kvar) * sizeof(T);
+  if (mode == 0) { shard = c->shard; nshards = c->nshards; }
+  const ShardRange sr = shard_range(a.g, shard, nshards);
+  const size_t set_bytes = (size_t)c->nx * nr_of(c->kvar) * sizeof(T);
+  a.pq0 = sr.pq0;
+  a.npq = sr.npq;
+  if (mode == 0) {
+    // partial reductions of this launch shape and arithmetic (all chunks when sharded): the buffer grows to the
+    // largest one used
+    const size_t pbytes = (size_t)std::max(sr.sets, nshards * sr.chunk) * set_bytes;
     if (c->part_bytes < pbytes) {
       lmdg::dfree(c->part);
       c->part = nullptr;
@@ -114,7 +143,7 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
       c->part_bytes = pbytes;
     }
   }
-  a.part = reinterpret_cast<T *>(c->part);
+  a.part = reinterpret_cast<T *>(mode == 0 ? c->part : ext);
   a.perm = c->perm;
   a.ytr = reinterpret_cast<T *>(c->ytr);
   a.ctrl = c->ctrl;
@@ -149,8 +178,9 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   if (store) {
     int kind = f64 ? 0 : (bf16 && c->variant != LMDG_STD ? 2 : 1);
     size_t per = c->variant == LMDG_STD ? 4 : 1;
-    size_t elems = (size_t)c->nang * c->nx * per;
-    const size_t bytes = elems * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
+    size_t elems = (size_t)c->nang * c->nx * per;   // user layout
+    // storage: one plane of wavefront-ordered slots per direction (lmdg::psi_plane)
+    const size_t bytes = (size_t)c->nang * lmdg::psi_plane(c->ni, c->nj) * per * (kind == 0 ? 8 : (kind == 1 ? 4 : 2));
     if (c->psi_bytes < bytes) {   // grown to the widest kind stored so far (cudaFree waits for earlier use)
       lmdg::dfree(c->psi);
       c->psi = nullptr;
@@ -163,6 +193,12 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     c->psi_elems = elems;
     a.psi = c->psi;
     a.psi_bf16 = kind == 2;
+  }
+  if (mode == 2) {
+    // epilogue from the caller's partial sets
+    CK(launch_epilogue<T>(c->kvar, c->nx, sr.sets, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
+                          c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
+    return 0;
   }
   if (!c->ev0) {
     CK(cudaEventCreate(&c->ev0));
@@ -179,13 +215,21 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     c->ytr_prec = want;
   }
   CK(cudaEventRecord(c->ev0, s));
-  CK(launch_sweep<T>(c->kvar, a, s));
+  if (a.npq > 0) CK(launch_sweep<T>(c->kvar, a, s));   // a shard beyond the last set sweeps nothing
   CK(cudaEventRecord(c->ev1, s));
   c->ev_pending = P;
   c->part_prec = P;
-  // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
-  CK(launch_epilogue<T>(c->kvar, c->nx, 4 * a.g.groups, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
-                        c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
+  if (mode == 0) {
+    if (nshards > 1) {
+      // every chunk from the other shards (the callback fills them in place, ordered on s)
+      if (!c->xfn) return LMDG_ERR_STATE;
+      if (c->xfn(c->xuser, c->part, (size_t)sr.chunk * set_bytes, nshards, X, sweep_flags(P, source, store), s) != 0)
+        return LMDG_ERR_EXCHANGE;
+    }
+    // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
+    CK(launch_epilogue<T>(c->kvar, c->nx, sr.sets, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
+                          c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
+  }
   if (P == 0) c->sweeps64++;
   else if (P == 1) c->sweeps32++;
   else c->sweeps2++;
@@ -487,6 +531,7 @@ const char *lmdg_strerror(int code) {
     case LMDG_ERR_TIMEOUT: return "sweep gave up waiting for an upstream strip (spin limit)";
     case LMDG_ERR_BREAKDOWN: return "non-finite residual or Krylov breakdown";
     case LMDG_ERR_STATE: return "call out of order";
+    case LMDG_ERR_EXCHANGE: return "the exchange callback of a sharded context failed";
     default: return "unknown error";
   }
 }
@@ -917,6 +962,63 @@ int lmdg_sweep(lmdg_ctx *c, const double *x, double *y, int flags, void *stream)
   return check_error_word(c, s);
 }
 
+int lmdg_shard_layout(const lmdg_ctx *c, int flags, int nshards, int *sets, int *chunk_sets, size_t *chunk_bytes) {
+  if (!c || nshards < 1 || nshards > 4096) return LMDG_ERR_ARG;
+  if ((flags & LMDG_SWEEP_FP32) && (flags & LMDG_SWEEP_F32X2)) return LMDG_ERR_ARG;
+  const int prec = (flags & LMDG_SWEEP_FP32) ? 1 : ((flags & LMDG_SWEEP_F32X2) ? 2 : 0);
+  const SweepGeom &g = prec == 0 ? c->g64 : (prec == 1 ? c->g32 : c->g2);
+  const ShardRange r = shard_range(g, 0, nshards);
+  const size_t word = prec == 1 ? sizeof(float) : (prec == 2 ? sizeof(f2) : sizeof(double));
+  if (sets) *sets = r.sets;
+  if (chunk_sets) *chunk_sets = r.chunk;
+  if (chunk_bytes) *chunk_bytes = (size_t)r.chunk * c->nx * nr_of(c->kvar) * word;
+  return 0;
+}
+
+int lmdg_sweep_shard(lmdg_ctx *c, const double *x, void *parts, int shard, int nshards, int flags, void *stream) {
+  if (!c || !x || !parts || nshards < 1 || nshards > 4096 || shard < 0 || shard >= nshards) return LMDG_ERR_ARG;
+  if (flags & (LMDG_HOST_PTRS | LMDG_SOLVE_EXACT_REF)) return LMDG_ERR_ARG;
+  if ((flags & LMDG_SWEEP_F32X2) && (flags & (LMDG_SWEEP_FP32 | LMDG_SWEEP_STORE))) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const int prec = (flags & LMDG_SWEEP_FP32) ? 1 : ((flags & LMDG_SWEEP_F32X2) ? 2 : 0);
+  const int bf16 = (prec == 1 && c->opt.precision == LMDG_FP32_BF16STORE) ? 1 : 0;
+  const int src = (flags & LMDG_SWEEP_SOURCE) ? 1 : 0;
+  const bool store = (flags & LMDG_SWEEP_STORE) != 0;
+  int e = prec == 1 ? do_sweep<float>(c, x, nullptr, src, store, bf16, s, 1, shard, nshards, parts)
+        : prec == 2 ? do_sweep<f2>(c, x, nullptr, src, false, 0, s, 1, shard, nshards, parts)
+                    : do_sweep<double>(c, x, nullptr, src, store, 0, s, 1, shard, nshards, parts);
+  if (e) return e;
+  return check_error_word(c, s);
+}
+
+int lmdg_sweep_combine(lmdg_ctx *c, const double *x, const void *parts, double *y, int flags, void *stream) {
+  if (!c || !x || !parts || !y) return LMDG_ERR_ARG;
+  if (flags & (LMDG_HOST_PTRS | LMDG_SWEEP_STORE | LMDG_SOLVE_EXACT_REF)) return LMDG_ERR_ARG;
+  if ((flags & LMDG_SWEEP_F32X2) && (flags & LMDG_SWEEP_FP32)) return LMDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(c->dev));
+  const int prec = (flags & LMDG_SWEEP_FP32) ? 1 : ((flags & LMDG_SWEEP_F32X2) ? 2 : 0);
+  const int src = (flags & LMDG_SWEEP_SOURCE) ? 1 : 0;
+  void *pp = const_cast<void *>(parts);
+  if (prec == 1) return do_sweep<float>(c, x, y, src, false, 0, s, 2, 0, 1, pp);
+  if (prec == 2) {
+    if (int e = ensure_f2(c, s)) return e;
+    return do_sweep<f2>(c, x, y, src, false, 0, s, 2, 0, 1, pp);
+  }
+  return do_sweep<double>(c, x, y, src, false, 0, s, 2, 0, 1, pp);
+}
+
+int lmdg_set_shard(lmdg_ctx *c, int shard, int nshards, lmdg_exchange_fn fn, void *user) {
+  if (!c || nshards < 1 || nshards > 4096 || shard < 0 || shard >= nshards) return LMDG_ERR_ARG;
+  if (nshards > 1 && !fn) return LMDG_ERR_ARG;
+  c->shard = nshards > 1 ? shard : 0;
+  c->nshards = nshards;
+  c->xfn = nshards > 1 ? fn : nullptr;
+  c->xuser = nshards > 1 ? user : nullptr;
+  return 0;
+}
+
 int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   if (!c || !psi) return LMDG_ERR_ARG;
   if (c->psi_kind < 0) return LMDG_ERR_STATE;
@@ -926,13 +1028,13 @@ int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   if (flags & LMDG_HOST_PTRS) {
     double *tmp = nullptr;
     if (lmdg::dmalloc(&tmp, sizeof(double) * c->psi_elems) != cudaSuccess) return LMDG_ERR_NOMEM;
-    cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s);
+    cudaError_t e1 = lmdg::psi_to_user(tmp, c->psi, c->psi_kind, per, c->ni, c->nj, c->nang, c->nq, c->perm, s);
     cudaError_t e2 = cudaMemcpyAsync(psi, tmp, sizeof(double) * c->psi_elems, cudaMemcpyDeviceToHost, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
     lmdg::dfree(tmp);
     return (e1 || e2 || e3) ? LMDG_ERR_CUDA : 0;
   }
-  CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->ni, c->nj, c->psi_elems, s));
+  CK(lmdg::psi_to_user(psi, c->psi, c->psi_kind, per, c->ni, c->nj, c->nang, c->nq, c->perm, s));
   return 0;
 }
 
@@ -1131,6 +1233,7 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
   if (!c || !g) return LMDG_ERR_ARG;
   if (c->variant == LMDG_RLM || c->variant == LMDG_P0 || c->q_layout == 2) return LMDG_ERR_ARG;
   if (!c->rev_ok) return LMDG_ERR_QUAD;
+  if (c->nshards > 1) return LMDG_ERR_STATE;   // the correlation reads the opposite directions' stored psi
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(c->dev));

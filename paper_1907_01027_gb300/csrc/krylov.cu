@@ -237,19 +237,23 @@ __global__ void fill_u32_kernel(unsigned *__restrict__ p, unsigned v, size_t N) 
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) p[k] = v;
 }
 
-// Stored angular unknowns to the user layout: the sweeps keep them column-major per direction, [u][i][j][per]
-// (a warp's 32 rows of one column contiguous); the user layout is row-major, [u][j][i][per], in double.
+// Stored angular unknowns to the user layout: the sweeps keep each direction's plane in its own wavefront order
+// (psi_slot in the quadrant's mirrored frame, per values a slot); the user layout is row-major, [u][j][i][per], in
+// double.  Item o runs over the sorted directions (quadrant = sorted index / nq), u = perm[sorted index].
 __global__ void psi_to_user_kernel(double *__restrict__ y, const void *__restrict__ x, int kind, int per, int ni,
-                                   int nj, size_t N) {
-  const size_t nx = (size_t)ni * nj;
+                                   int nj, int nang, int nq, const int *__restrict__ perm) {
+  const size_t nx = (size_t)ni * nj, N = (size_t)nang * nx * per, plane = psi_plane(ni, nj);
   for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < N; o += (size_t)gridDim.x * blockDim.x) {
     const size_t c = o % per, cell = o / per;
-    const size_t u = cell / nx, K = cell - u * nx;
-    const size_t j = K / ni, i = K - j * ni;
-    const size_t k = (u * nx + i * nj + j) * per + c;
-    if (kind == 1) y[o] = (double)reinterpret_cast<const float *>(x)[k];
-    else if (kind == 2) y[o] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
-    else y[o] = reinterpret_cast<const double *>(x)[k];
+    const size_t ks = cell / nx, K = cell - ks * nx;
+    const int j = (int)(K / ni), i = (int)(K - (size_t)j * ni);
+    const int quad = (int)ks / nq, u = perm[ks];
+    const int lx = (quad == 0 || quad == 3) ? i : ni - 1 - i, lr = quad <= 1 ? j : nj - 1 - j;
+    const size_t k = ((size_t)u * plane + psi_slot(ni, lx, lr)) * per + c;
+    const size_t out = ((size_t)u * nx + K) * per + c;
+    if (kind == 1) y[out] = (double)reinterpret_cast<const float *>(x)[k];
+    else if (kind == 2) y[out] = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(x)[k]);
+    else y[out] = reinterpret_cast<const double *>(x)[k];
   }
 }
 
@@ -396,9 +400,11 @@ cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s) {
   fill_u32_kernel<<<grid_for(N), 256, 0, s>>>(p, v, N);
   return cudaGetLastError();
 }
-cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int ni, int nj, size_t N, cudaStream_t s) {
+cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int ni, int nj, int nang, int nq, const int *perm,
+                        cudaStream_t s) {
+  const size_t N = (size_t)nang * ni * nj * per;
   add_launches(1);
-  psi_to_user_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, per, ni, nj, N);
+  psi_to_user_kernel<<<grid_for(N), 256, 0, s>>>(y, x, kind, per, ni, nj, nang, nq, perm);
   return cudaGetLastError();
 }
 

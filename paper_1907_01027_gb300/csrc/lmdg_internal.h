@@ -31,6 +31,16 @@ struct SweepGeom {
 };
 
 constexpr int kMaxA = 4;        // cap on directions per warp (template instances 1..4)
+
+// Stored angular unknowns of one direction are kept in its sweep's wavefront order: the cell in local column x
+// and local row r (the quadrant's mirrored frame) sits at slot ((r / 32) (ni + 31) + x + r % 32) 32 + r % 32, so
+// the 32 lanes of a warp, which solve the cells (t - k, 32 s + k) of strip s at step t, store to 32 consecutive
+// slots.  A plane holds strips x (ni + 31) x 32 slots, the ones outside the mesh unused.
+__host__ __device__ inline size_t psi_plane(int ni, int nj) { return (size_t)((nj + 31) / 32) * (ni + 31) * 32; }
+__host__ __device__ inline size_t psi_slot(int ni, int x, int r) {
+  const int l = r & 31;
+  return ((size_t)(r >> 5) * (ni + 31) + x + l) * 32 + l;
+}
 #ifndef LMDG_CHUNK
 #define LMDG_CHUNK 8
 #endif
@@ -58,8 +68,10 @@ struct SweepArgs {
   const T *p1ra;       // [nx][3] P1 r_alpha (RLMDG, source sweeps) or null
   int source;          // 1: add eps q and the inflow data alpha
   T *part;             // [4*groups][nx][NR] partial reductions, written once each
-  void *psi;           // storing sweep output or null: [nang (user order, through perm)][ni (column i)][nj (row j)]
-                       // [4 standard, 1 low-memory], column-major cells so that a warp's stores coalesce
+  int pq0, npq;        // the launch sweeps the partial sets [pq0, pq0 + npq) (quadrant * groups + group): all
+                       // 4*groups of them, or one shard's range when the directions are split across GPUs
+  void *psi;           // storing sweep output or null: [nang (user order, through perm)][psi_plane slots in the
+                       // direction's wavefront order, psi_slot][4 standard, 1 low-memory], so a warp's stores coalesce
   int psi_bf16;        // psi is __nv_bfloat16 (low-memory variants only)
   const int *perm;     // [nang] sorted index -> user index
   T *ytr;              // [nang][strips][ni][kTraceStride] strip-boundary traces, kTraceEmpty when unwritten
@@ -67,7 +79,8 @@ struct SweepArgs {
   long long spin_limit;
   const T *cellsrc;    // [nx][4] per-cell source moments / isotropic slopes of this sweep (prep_kernel)
   const T *cellsh;     // [nx] sigma_t h
-  const double *corr;  // adjoint correlation mode: stored forward psi (layout of psi, double); the reduction
+  const double *corr;  // adjoint correlation mode: stored forward psi (layout of psi, double; each plane in the
+                       // wavefront order of its own, the opposite, quadrant); the reduction
                        // becomes sum_l w_l u_l,r psi_rev(l),r (r = 0 only for LMDG)
   const int *rev;      // [nang] sorted index -> user index of the opposite direction (corr mode)
   // Coefficient tables (FP64 sweeps; null: coefficients computed in the kernel).  With them, cellsh carries the
@@ -228,4 +241,9 @@ struct lmdg_ctx {
   lmdg::VertexDsa dsa;                     // vertex diffusion correction (precond = 2, 3)
   double *binv = nullptr;                  // precond = 3: [nx][4][4] inverses of K's cell-diagonal blocks
   int local_mode = 0;                      // FP64 sweeps cut the upwind coupling (SweepArgs::local)
+  // angle sharding (lmdg_set_shard): this context sweeps chunk `shard` of `nshards` of the partial sets and
+  // xfn fills the other chunks before every epilogue
+  int shard = 0, nshards = 1;
+  lmdg_exchange_fn xfn = nullptr;
+  void *xuser = nullptr;
 };

@@ -142,6 +142,8 @@ extern "C" int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, con
   a.p1ra = nullptr;
   a.source = 0;
   a.part = reinterpret_cast<double *>(base + off_part);
+  a.pq0 = 0;
+  a.npq = 4 * g.groups;
   a.psi = nullptr;
   a.psi_bf16 = 0;
   a.perm = reinterpret_cast<const int *>(base);

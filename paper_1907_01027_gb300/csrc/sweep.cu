@@ -423,9 +423,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   }
   __syncthreads();
   const int unit = s_unit;
-  const int per_strip = 4 * A.g.groups;
+  const int per_strip = A.npq;                      // partial sets of this launch (tickets strip-major)
   const int strip = unit / per_strip;
-  const int pq = unit - strip * per_strip;          // partial index = quadrant * groups + group
+  const int pq = A.pq0 + (unit - strip * per_strip);   // partial index = quadrant * groups + group
   const int quad = pq / A.g.groups, grp = pq - quad * A.g.groups;
   const int sx = (quad == 0 || quad == 3) ? 1 : -1;
   const int sy = (quad <= 1) ? 1 : -1;
@@ -514,6 +514,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
   }
   const int nsteps = ni + 31;
   const int nchunks = (nsteps + C - 1) / C;
+  const size_t plane = psi_plane(ni, nj);   // slots per direction of the stored psi
 
   // cell data of chunk cc -> buffer cc & 1 (item = (step, lane) of the chunk)
   auto stage = [&](int cc) {
@@ -594,9 +595,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
         const bool act = row_ok && x >= 0 && x < ni;
         const int i = sx > 0 ? x : ni - 1 - x;
         const int K = act ? j * ni + i : 0;
-        // stored angular unknowns (and the adjoint's correlation input) are column-major, [i][j]: the warp's 32
-        // rows of one column are contiguous, so its psi stores coalesce
-        const int Kt = act ? i * nj + j : 0;
+        // stored angular unknowns in wavefront order (psi_slot): this step's 32 cells are consecutive slots, so a
+        // warp's psi stores coalesce; the adjoint's correlation input is the opposite direction's plane, whose
+        // frame is this one mirrored in both axes
+        const size_t pslot = ((size_t)strip * nsteps + t) * 32 + lane;
+        const size_t rslot = use_corr && act ? psi_slot(ni, ni - 1 - x, nj - 1 - row) : 0;
         const bool xbnd = (x == 0);
         const bool ybnd = (strip == 0 && lane == 0);
         const T *yws = yup + ((size_t)warp * APW * C + s) * NS;   // + k * C * NS: direction k's inflow (lane 0)
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 if (use_corr) {
                   // adjoint correlation: this sweep's psi (the multiplier of the opposite direction) times the
                   // stored forward psi of that opposite direction, per Legendre moment
-                  const double *pf = A.corr + ((size_t)cA[k] * nx + Kt) * 4;
+                  const double *pf = A.corr + ((size_t)cA[k] * plane + rslot) * 4;
                   acc[0] += wl * u0 * (T)pf[0];
                   acc[1] += Wx[k] * u1 * (T)pf[1];
                   acc[2] += Wy[k] * u2 * (T)pf[2];
@@ -743,7 +746,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-                if (!LEAN && A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * nx + Kt) * 4, u0, flip(u1, mx), flip(u2, my),
+                if (!LEAN && A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * plane + pslot) * 4, u0, flip(u1, mx), flip(u2, my),
                                          flip(u3, mxy));
               } else if constexpr (VAR == 1 || P0) {
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
@@ -755,7 +758,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 // direction-dependent part of L(u; b_1), L(u; b_2): 2a (U0 - u0), 2b (V0 - u0) (zero inflow traces
                 // outside the mesh)
                 if (use_corr) {
-                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                  acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * plane + rslot];
                 } else {
                   acc[0] = fma(wl, u0, acc[0]);
                   if constexpr (!P0) {
@@ -771,7 +774,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   ys[k][0] = u0 + A2;
                   ys[k][1] = A13;
                 }
-                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
+                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
               } else {
                 // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
                 //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
@@ -814,7 +817,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   // and rides on the traces' slopes (U1, V1); row 0 does not see it
                   const T rec3 = ybnd ? rec1 - ya1 : (T)0.5 * (rec1 - yin[3]);
                   if (use_corr) {
-                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * plane + rslot];
                   } else {
                     acc[0] = fma(wl, u0, acc[0]);
                     acc[1] = fma(nWxb[k], V1 - rec3, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
@@ -828,7 +831,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1 + rec3; ys[k][2] = u0; ys[k][3] = rec1;
                 } else {
                   if (use_corr) {
-                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * nx + Kt];
+                    acc[0] += wl * u0 * (T)A.corr[(size_t)cA[k] * plane + rslot];
                   } else {
                     acc[0] = fma(wl, u0, acc[0]);
                     acc[1] = fma(nWxb[k], V1, fma(Dx[k], rec1, fma(Wx[k], U0 - u0, acc[1])));
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
                   ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 }
-                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * nx + Kt, u0, A.psi_bf16);
+                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
                 T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * ni + x) * kTraceStride;
@@ -1096,7 +1099,8 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   SweepArgs<T> args = a;
   void *params[] = {&args};
   add_launches(1);
-  e = cudaLaunchKernel(k, dim3(a.g.units()), dim3(a.g.warps * 32), params, smem, s);
+  if (a.npq < 1 || a.pq0 < 0 || a.pq0 + a.npq > 4 * a.g.groups) return cudaErrorInvalidValue;
+  e = cudaLaunchKernel(k, dim3(a.g.strips * a.npq), dim3(a.g.warps * 32), params, smem, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
