@@ -400,6 +400,8 @@ def run_gpu(args, rank, ws, dist):
     # correction (precond = 2), time to 1e-8 with FP32 sweeps and FP64 residual sweeps against the FP64 solver
     if not args.skip_diffusive:
         out["gmres_time_to_1e-8_eps1e-3"] = diffusive_times(args, local)
+    if not args.skip_configs:
+        out["other_configs"] = other_configs(local)
 
     # end to end through the public API with host buffers: setup from host arrays, solve, phi back to host; the
     # host arrays (the problem's cross sections, source and quadrature, and phi) live in pinned memory
@@ -496,6 +498,61 @@ def diffusive_times(args, local):
     return res
 
 
+def other_configs(local):
+    """The workload configurations besides the benchmark's own, timed on the GPU (one solve each after a warm-up
+    solve in the same context; CUDA events): the 32^2 S4 FP64 case to 1e-10 (GMRES; source iteration is not
+    built), the 256^2 S8 diffusion-limit sweep (Q1-DG against LMDG, FP64, to 1e-8; the vertex correction with the
+    cell-block step for eps < 1), the 512^2 S12 block medium (RLMDG, FP64 and mixed to 1e-8) and the adjoint
+    workload (256^2 S8 bumps: Q1-DG and LMDG gradients, FP64 and mixed)."""
+    import numpy as np
+    import torch
+    from paper_1907_01027_gb300 import Context, FP32, FP64, RESID_F32X2
+    from workloads.problems import config1, config2, config3, config5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed_solve(p, variant, **kw):
+        ctx = Context(p, variant, device=local, **kw)
+        ctx.solve(want_x=False, want_phi=True, device=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.close()
+        return {"ms": e0.elapsed_time(e1), "status": rc, "iters": st["iters"], "resid": st["resid"] / st["resid0"],
+                "updates_per_s": (st["sweeps_fp64"] + st["sweeps_fp32"] + st["sweeps_f32x2"]) * p.nx * p.nang /
+                (e0.elapsed_time(e1) / 1e3)}
+
+    out = {}
+    p1 = config1()
+    out["32x32_S4_fp64_to_1e-10"] = {v: timed_solve(p1, v, precision=FP64, tol=1e-10) for v in VARIANTS}
+    out["256x256_S8_fp64_to_1e-8"] = {}
+    for eps in (1.0, 1e-2, 1e-4):
+        p2 = config2(eps=eps)
+        kw = dict(precision=FP64, tol=1e-8, max_iters=3000)
+        if eps < 1:
+            kw["precond"] = 3
+        out["256x256_S8_fp64_to_1e-8"][f"eps={eps:g}"] = {v: timed_solve(p2, v, **kw) for v in ("std", "lm")}
+    p3 = config3()
+    out["512x512_S12_blocks_rlm_to_1e-8"] = {
+        "fp64": timed_solve(p3, "rlm", precision=FP64, tol=1e-8, max_iters=5000),
+        "mixed": timed_solve(p3, "rlm", precision=FP32, resid=RESID_F32X2, tol=1e-8, max_iters=5000)}
+    p5 = config5()
+    g = np.ascontiguousarray(p5.info["detector"])
+    adj = {}
+    for v in ("std", "lm"):
+        for mode, kw in (("fp64", dict(precision=FP64)), ("mixed", dict(precision=FP32))):
+            ctx = Context(p5, v, tol=1e-10, device=local, **kw)
+            ctx.adjoint(g)
+            t = time.perf_counter()
+            J, _, _, _, st = ctx.adjoint(g)
+            adj[f"{v}_{mode}"] = {"ms": 1e3 * (time.perf_counter() - t), "J": J, "iters": st["iters"]}
+            ctx.close()
+    out["256x256_S8_adjoint_gradients"] = adj
+    return out
+
+
 def run_profile(args):
     """Small case for ncu: 512x512 cells, S16, the bench media; per pass the three FP32 non-storing sweeps (as
     inside GMRES: Q1-DG, LMDG, RLMDG), an FP32 Q1-DG storing sweep (psi 604 MB, larger than L2), the three
@@ -533,6 +590,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-diffusive", action="store_true", help="leave out the eps = 1e-3 solves")
+    ap.add_argument("--skip-configs", action="store_true", help="leave out the other workload configurations")
     ap.add_argument("--profile", action="store_true", help="small fixed case for ncu captures")
     args = ap.parse_args()
     if args.profile:

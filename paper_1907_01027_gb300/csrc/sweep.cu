@@ -392,7 +392,9 @@ cudaError_t build_coef_tables(int variant, int nmat, int ncls, const double *mat
 // instances only), else they are formed in the kernel from sigma_t h.  LEAN: a non-storing sweep without inflow
 // data, angle-dependent source or correlation (the GMRES iterations; the residual sweeps of problems with vacuum
 // inflow and isotropic source), compiled without the per-step tests for them (FP32 and float-float instances).
-template <typename T, int VAR, int APW, bool TAB, bool LEAN>
+// LSTORE (with LEAN; FP32, one or two directions per warp): the same sweep storing the angular unknowns
+// unconditionally -- the recovery sweep of a vacuum, isotropic-source problem.
+template <typename T, int VAR, int APW, bool TAB, bool LEAN, bool LSTORE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_kernel(const SweepArgs<T> A) {
   constexpr bool P0 = VAR == kP0;         // P0-DG: the LMDG row-0 solve without slopes
   constexpr bool Q1R = VAR == kRlmQ1;     // RLMDG with the Q1-type reconstruction (the xi eta term)
@@ -746,7 +748,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                 }
                 xs[k][0] = u0 + u1; xs[k][1] = u2 + u3;
                 ys[k][0] = u0 + u2; ys[k][1] = u1 + u3;
-                if (!LEAN && A.psi) store_psi4<T>(A.psi, ((size_t)uA[k] * plane + pslot) * 4, u0, flip(u1, mx), flip(u2, my),
+                if (LSTORE || (!LEAN && A.psi)) store_psi4<T>(A.psi, ((size_t)uA[k] * plane + pslot) * 4, u0, flip(u1, mx), flip(u2, my),
                                          flip(u3, mxy));
               } else if constexpr (VAR == 1 || P0) {
                 // ---------------- LMDG: row 0 of L00 for u0; u1..3 = A1..3 (isotropic)
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   ys[k][0] = u0 + A2;
                   ys[k][1] = A13;
                 }
-                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
+                if (LSTORE || (!LEAN && A.psi)) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
               } else {
                 // ---------------- RLMDG: row 0 of Ltilde00 with the upwind reconstruction
                 //   slopes (h/2) delta of u0: (u0 - u0_up)/2 inside, u0 - alpha_mid on an inflow face, 0 across
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LMDG_MINB32 : 1) sweep_k
                   xs[k][0] = u0 + A1 + rec1; xs[k][1] = A23 + rec2; xs[k][2] = u0;
                   ys[k][0] = u0 + A2 + rec2; ys[k][1] = A13 + rec1; ys[k][2] = u0;
                 }
-                if (!LEAN && A.psi) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
+                if (LSTORE || (!LEAN && A.psi)) store_psi0<T>(A.psi, (size_t)uA[k] * plane + pslot, u0, A.psi_bf16);
               }
               if (lane == 31 && has_above) {
                 T *yp = A.ytr + (((size_t)ang[k] * A.g.strips + strip) * ni + x) * kTraceStride;
@@ -998,42 +1000,48 @@ __global__ void epilogue_kernel(int nx, int P, double h, const T *__restrict__ p
   *reinterpret_cast<double2 *>(y + 4 * (size_t)K + 2) = make_double2(o2, o3);
 }
 
-template <typename T, int VAR, int APW, bool TAB, bool LEAN>
+template <typename T, int VAR, int APW, bool TAB, bool LEAN, bool LSTORE>
 static const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW, TAB, LEAN>);
+  return reinterpret_cast<const void *>(&sweep_kernel<T, VAR, APW, TAB, LEAN, LSTORE>);
 }
 
-template <typename T, int VAR, bool TAB, bool LEAN>
+template <typename T, int VAR, bool TAB, bool LEAN, bool LSTORE>
 static const void *kernel_for(int apw) {
-  // float-float sweeps: one or two directions per warp (choose_geom caps them there)
-  if constexpr (is_f2<T>::value) {
-    return apw == 1 ? kernel_ptr<T, VAR, 1, TAB, LEAN>() : kernel_ptr<T, VAR, 2, TAB, LEAN>();
+  // float-float sweeps and the lean storing instances: one or two directions per warp (choose_geom's FP32 and
+  // float-float shapes)
+  if constexpr (is_f2<T>::value || LSTORE) {
+    return apw == 1 ? kernel_ptr<T, VAR, 1, TAB, LEAN, LSTORE>() : kernel_ptr<T, VAR, 2, TAB, LEAN, LSTORE>();
   } else {
     switch (apw) {
-      case 1: return kernel_ptr<T, VAR, 1, TAB, LEAN>();
-      case 2: return kernel_ptr<T, VAR, 2, TAB, LEAN>();
-      case 3: return kernel_ptr<T, VAR, 3, TAB, LEAN>();
-      default: return kernel_ptr<T, VAR, 4, TAB, LEAN>();
+      case 1: return kernel_ptr<T, VAR, 1, TAB, LEAN, false>();
+      case 2: return kernel_ptr<T, VAR, 2, TAB, LEAN, false>();
+      case 3: return kernel_ptr<T, VAR, 3, TAB, LEAN, false>();
+      default: return kernel_ptr<T, VAR, 4, TAB, LEAN, false>();
     }
   }
 }
 
-template <typename T, bool TAB, bool LEAN>
+template <typename T, bool TAB, bool LEAN, bool LSTORE = false>
 static const void *kernel_for_variant(int variant, int apw) {
   switch (variant) {
-    case LMDG_STD: return kernel_for<T, 0, TAB, LEAN>(apw);
-    case LMDG_LM: return kernel_for<T, 1, TAB, LEAN>(apw);
-    case LMDG_RLM: return kernel_for<T, 2, TAB, LEAN>(apw);
-    case kRlmStar: return kernel_for<T, 3, TAB, LEAN>(apw);
-    case kRlmQ1: return kernel_for<T, kRlmQ1, TAB, LEAN>(apw);
-    default: return kernel_for<T, kP0, TAB, LEAN>(apw);
+    case LMDG_STD: return kernel_for<T, 0, TAB, LEAN, LSTORE>(apw);
+    case LMDG_LM: return kernel_for<T, 1, TAB, LEAN, LSTORE>(apw);
+    case LMDG_RLM: return kernel_for<T, 2, TAB, LEAN, LSTORE>(apw);
+    case kRlmStar: return kernel_for<T, 3, TAB, LEAN, LSTORE>(apw);
+    case kRlmQ1: return kernel_for<T, kRlmQ1, TAB, LEAN, LSTORE>(apw);
+    default: return kernel_for<T, kP0, TAB, LEAN, LSTORE>(apw);
   }
 }
 
-// coefficient tables exist for the FP64 and float-float sweeps; lean instances for FP32 and float-float
+// coefficient tables exist for the FP64 and float-float sweeps; lean instances for FP32 and float-float, lean
+// storing ones for FP32 with one or two directions per warp
 template <typename T>
-static const void *sweep_kernel_ptr(int variant, int apw, bool tab, bool lean) {
+static const void *sweep_kernel_ptr(int variant, int apw, bool tab, bool lean, bool lstore = false) {
   constexpr bool kLean = !std::is_same<T, double>::value;
+  if constexpr (std::is_same<T, float>::value) {
+    if (lstore && apw <= 2) return kernel_for_variant<T, false, true, true>(variant, apw);
+  }
+  (void)lstore;
   if constexpr (sizeof(T) == 8) {
     if (tab) {
       if constexpr (kLean) {
@@ -1091,8 +1099,9 @@ cudaError_t launch_sweep(int variant, const SweepArgs<T> &a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // lean: nothing a lean instance leaves out is needed -- a source sweep without inflow data or angle-dependent
   // source (its source enters through prep_kernel's cell data) runs the same per-step code as a homogeneous one
-  const bool lean = !(a.source && (a.pd.alpha != nullptr || a.q_per_angle)) && a.psi == nullptr && a.corr == nullptr;
-  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr, lean);
+  const bool plain = !(a.source && (a.pd.alpha != nullptr || a.q_per_angle)) && a.corr == nullptr;
+  const bool lean = plain && a.psi == nullptr;
+  const void *k = sweep_kernel_ptr<T>(variant, a.g.apw, a.coef != nullptr, lean, plain && a.psi != nullptr);
   const size_t smem = sweep_smem_bytes<T>(variant, a.g.warps, a.g.apw);
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -112,15 +112,17 @@ def test_mixed_precision_diffusive(variant):
                                               ("rlm", (13, 24), 1e-2, {})])
 def test_block_precond_apply_matches_oracle(variant, n, eps, kw):
     """y = B^-1 x + C(J x) on the device (blocks from the FP64 sweeps without upwind coupling) against the
-    oracle's (blocks by probing its reduced operator, one V-cycle); square and rectangular meshes (the first rows
-    of the square medium)."""
+    oracle's (blocks by probing its reduced operator, one V-cycle); square and rectangular meshes (the lower left
+    n_x x n_y corner of a square medium)."""
     from oracle.vdsa import diagonal_blocks
     if isinstance(n, tuple):
-        p = _medium(n[0], eps)
-        ny = n[1]
-        p.ny = ny
-        p.sigma_s, p.sigma_a, p.q = p.sigma_s[:n[0] * ny].copy(), p.sigma_a[:n[0] * ny].copy(), p.q[:n[0] * ny].copy()
-        n = n[0]
+        ni, nj = n
+        m = max(ni, nj)
+        p = _medium(m, eps)
+        p.n, p.ny = ni, nj
+        corner = lambda a: np.ascontiguousarray(a.reshape(m, m, *a.shape[1:])[:nj, :ni].reshape(ni * nj, *a.shape[1:]))
+        p.sigma_s, p.sigma_a, p.q = corner(p.sigma_s), corner(p.sigma_a), corner(p.q)
+        n = ni
     else:
         p = _medium(n, eps)
     so = SweepOracle(p, suppress=bool(kw.get("suppress")))
