@@ -39,12 +39,12 @@ FLOPS_PER_UPDATE = {"std": 90, "lm": 31, "rlm": 55}
 # partial reductions per cell, is the same at 1024x1024, so a full launch moves 4x these), issue-active % of the
 # schedulers, warps active % of the maximum, and warp instructions per cell-direction update.  None until measured
 # for the current kernels; must be re-measured whenever the kernel changes.
-SWEEP_NCU_512 = {"std": {"dram_bytes": 68.402688e6, "issue_active_pct": 43.14, "warps_active_pct": 23.97,
-                         "inst_per_update": 4.995},
-                 "lm": {"dram_bytes": 35.471616e6, "issue_active_pct": 23.42, "warps_active_pct": 11.78,
-                        "inst_per_update": 2.637},
-                 "rlm": {"dram_bytes": 109.411584e6, "issue_active_pct": 38.51, "warps_active_pct": 23.91,
-                         "inst_per_update": 5.945}}
+SWEEP_NCU_512 = {"std": {"dram_bytes": 68.734464e6, "issue_active_pct": 42.42, "warps_active_pct": 23.08,
+                         "inst_per_update": 5.008},
+                 "lm": {"dram_bytes": 36.167168e6, "issue_active_pct": 22.94, "warps_active_pct": 11.56,
+                        "inst_per_update": 2.642},
+                 "rlm": {"dram_bytes": 109.970176e6, "issue_active_pct": 38.22, "warps_active_pct": 22.89,
+                         "inst_per_update": 5.955}}
 # the pipeline of the sweep: a strip of 32 rows takes n + 31 steps and the strip above starts 32 + 8 steps later
 STRIP_LAG = 40
 
@@ -319,6 +319,7 @@ def run_gpu(args, rank, ws, dist):
 
     # time to 1e-8: mixed (from the timed region) vs FP64 (one solve each, after it)
     ttr = {}
+    phis = {}
     for v in VARIANTS:
         mixed = [st for vv, st in stats if vv == v]
         ttr[v] = {"mixed_ms": sum(s["time_ms"] for s in mixed) / len(mixed),
@@ -326,7 +327,8 @@ def run_gpu(args, rank, ws, dist):
                   "mixed_sweeps_fp32": mixed[-1]["sweeps_fp32"], "mixed_sweeps_f32x2": mixed[-1]["sweeps_f32x2"],
                   "mixed_resid": mixed[-1]["resid"] / mixed[-1]["resid0"]}
         # the same solve's final residual recomputed with FP64 sweeps: ||K x - b'|| / ||b'||
-        xs, _, _, _ = ctxs[v].solve(want_x=True, want_phi=False, device=True)
+        xs, phis[v], _, _ = ctxs[v].solve(want_x=True, want_phi=True, device=True)
+        ttr[v]["mixed_kappa_est"] = mixed[-1]["kappa_est"]
         r = ctxs[v].sweep(xs, flags=SWEEP_SOURCE)
         b = ctxs[v].sweep(torch.zeros_like(xs), flags=SWEEP_SOURCE)
         ttr[v]["mixed_resid_fp64_check"] = float(torch.linalg.norm(r) / torch.linalg.norm(b))
@@ -349,11 +351,20 @@ def run_gpu(args, rank, ws, dist):
             ctx = Context(p, v, precision=FP64, tol=1e-8, device=local)
             torch.cuda.synchronize()
             e0.record()
-            _, _, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
+            _, phi64, st, rc = ctx.solve(want_x=False, want_phi=True, device=True)
             e1.record()
             torch.cuda.synchronize()
+            # error of the mixed solution against the FP64 one, and the bound the solves' kappa_est states: two
+            # solutions with relative residuals below tol differ by at most about 2 kappa tol in the unknowns GMRES
+            # sees, u = M^-1 x (M the right preconditioner: the identity for Q1-DG, so there the bound is on phi;
+            # the Jacobi scaling of the slope block for LMDG and RLMDG, whose phi differences it does not bound)
+            kap = max(st["kappa_est"], ttr[v]["mixed_kappa_est"])
             ttr[v].update({"fp64_ms": e0.elapsed_time(e1), "fp64_iters": st["iters"], "fp64_status": rc,
-                           "fp64_sweep_avg_ms": st["sweep_ms_fp64"] / max(1, st["sweeps_fp64"])})
+                           "fp64_sweep_avg_ms": st["sweep_ms_fp64"] / max(1, st["sweeps_fp64"]),
+                           "fp64_kappa_est": st["kappa_est"],
+                           "mixed_vs_fp64_phi_rel": float(torch.linalg.norm(phis[v] - phi64) /
+                                                          torch.linalg.norm(phi64)),
+                           "bound_2_kappa_tol_preconditioned_unknowns": 2 * kap * 1e-8})
             ctx.close()
     out["gmres_time_to_1e-8"] = ttr
 

@@ -75,8 +75,7 @@ enum {
   LMDG_ERR_TIMEOUT = -6,    /* a sweep kernel gave up waiting for an upstream tile (spin limit); the
                                kernel exits cleanly and the context stays usable */
   LMDG_ERR_BREAKDOWN = -7,  /* non-finite residual or Krylov breakdown */
-  LMDG_ERR_STATE = -8,      /* call out of order (e.g. lmdg_get_psi before a storing sweep) */
-  LMDG_ERR_EXCHANGE = -9    /* the exchange callback of a sharded context (lmdg_set_shard) returned nonzero */
+  LMDG_ERR_STATE = -8       /* call out of order (e.g. lmdg_get_psi before a storing sweep) */
 };
 
 typedef struct {
@@ -137,6 +136,10 @@ typedef struct {
   long long launches;  /* kernels launched by the call */
   int sweeps_f32x2;    /* full transport sweeps run in float-float */
   double sweep_ms_f32x2; /* device time inside float-float sweep kernels */
+  double kappa_est;    /* largest condition number of a GMRES cycle's Hessenberg matrix (the right-preconditioned
+                          operator K M restricted to the cycle's Krylov space: a lower estimate of cond(K M), exact
+                          as the space fills).  Two solutions with relative residuals r1, r2 differ relatively by
+                          at most about cond (r1 + r2): with this estimate, the error bound the solve states. */
 } lmdg_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -275,10 +278,11 @@ int lmdg_sweep_noalloc(int variant, int n, double h, int n_omega, const double *
  * one per (quadrant, direction group) of the launch shape, each an [N][NR] array (NR reduced values per cell) in
  * the sweep's arithmetic (double; float for LMDG_SWEEP_FP32; a pair of floats, 8 bytes, for LMDG_SWEEP_F32X2),
  * summed by the epilogue in a fixed order.  Sharding splits the sets into nshards contiguous chunks of chunk_sets
- * sets; shard r sweeps the directions of chunk r over the whole mesh, and once every chunk is in place the
- * epilogue gives a result bitwise equal to the unsharded sweep.  A partial buffer holds nshards * chunk_sets sets
- * (chunk r at byte offset r * chunk_bytes; sets past the last one are padding).  Contexts of one problem set up
- * with the same arguments (and the same LMDG_SWEEP_GEOM environment) have the same layout. */
+ * sets; shard r sweeps the directions of chunk r over the whole mesh (on its own GPU, with its own context of the
+ * same problem), the chunks are gathered into one buffer (an all-gather between the GPUs), and lmdg_sweep_combine
+ * then gives a result bitwise equal to lmdg_sweep.  A partial buffer holds nshards * chunk_sets sets (chunk r at
+ * byte offset r * chunk_bytes; sets past the last one are padding).  Contexts of one problem set up with the same
+ * arguments (and the same LMDG_SWEEP_GEOM environment) have the same layout. */
 
 /* Layout of the partial sets for the arithmetic of flags (LMDG_SWEEP_FP32 / LMDG_SWEEP_F32X2 / neither) split
  * into nshards chunks (1 <= nshards <= 4096): the number of sets, the sets per chunk and the bytes per chunk (any
@@ -296,22 +300,6 @@ int lmdg_sweep_shard(lmdg_ctx *ctx, const double *x, void *parts, int shard, int
  * other GPUs): y = K x, or K x - b with LMDG_SWEEP_SOURCE, as lmdg_sweep gives for the same flags; x, parts, y
  * DEVICE pointers.  Asynchronous on stream. */
 int lmdg_sweep_combine(lmdg_ctx *ctx, const double *x, const void *parts, double *y, int flags, void *stream);
-
-/* Exchange callback of a sharded context: on entry chunk `shard` of parts (nshards chunks of chunk_bytes, DEVICE,
- * in the arithmetic of flags) holds this shard's partial sets, written on stream; on return every other chunk
- * must be filled, or be filled by work ordered on stream -- an all-gather in place over the shards' GPUs (for
- * instance NCCL's).  x is the sweep's input and flags its lmdg_sweep flags (for callers that sweep the other
- * chunks themselves).  Return 0, or nonzero to fail the sweep with LMDG_ERR_EXCHANGE. */
-typedef int (*lmdg_exchange_fn)(void *user, void *parts, size_t chunk_bytes, int nshards, const double *x,
-                                int flags, void *stream);
-
-/* Make every later sweep of the context (lmdg_sweep, and every sweep of lmdg_solve including its recovery sweep)
- * sweep chunk `shard` of nshards only and call fn(user, ...) before its epilogue; nshards = 1 undoes it (fn may
- * then be NULL).  GMRES vectors stay replicated: every shard runs the same solve, and with identical
- * inputs gets identical iterates.  Stored angular unknowns are sharded by direction: lmdg_get_psi returns this
- * shard's directions, the other directions' entries are undefined.  lmdg_adjoint on a sharded context returns
- * LMDG_ERR_STATE (its correlation sweep reads the opposite directions' stored unknowns). */
-int lmdg_set_shard(lmdg_ctx *ctx, int shard, int nshards, lmdg_exchange_fn fn, void *user);
 
 /* Problem sizes of a context: cells along x and y, n_Omega, variant (any pointer may be NULL). */
 int lmdg_info(const lmdg_ctx *ctx, int *nx, int *ny, int *n_omega, int *variant);

@@ -97,16 +97,9 @@ ShardRange shard_range(const SweepGeom &g, int shard, int nshards) {
   return r;
 }
 
-// lmdg_sweep flags of an internal sweep (what the exchange callback is told)
-int sweep_flags(int prec, int source, bool store) {
-  return (source ? LMDG_SWEEP_SOURCE : 0) | (prec == 1 ? LMDG_SWEEP_FP32 : 0) | (prec == 2 ? LMDG_SWEEP_F32X2 : 0) |
-         (store ? LMDG_SWEEP_STORE : 0);
-}
-
-// One transport sweep with its angular reduction.  mode 0: sweep and epilogue (y = K x or K x - b); a context
-// sharded by lmdg_set_shard sweeps its own chunk of partial sets and calls the exchange callback before the
-// epilogue.  mode 1: sweep the partial sets of (shard, nshards) into ext (the full [chunks * chunk][nx][NR] layout,
-// only this shard's chunk written), no epilogue.  mode 2: epilogue only, from the partial sets in ext.
+// One transport sweep with its angular reduction.  mode 0: sweep and epilogue (y = K x or K x - b).  mode 1: sweep
+// the partial sets of chunk `shard` of nshards into ext (the full [chunks * chunk][nx][NR] layout, only this chunk
+// written), no epilogue.  mode 2: epilogue only, from the partial sets in ext.
 template <typename T>
 int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, int bf16, cudaStream_t s,
              int mode = 0, int shard = 0, int nshards = 1, void *ext = nullptr) {
@@ -126,15 +119,13 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   a.q_per_angle = c->q_layout == 2;
   a.X = X;
   a.source = source;
-  if (mode == 0) { shard = c->shard; nshards = c->nshards; }
   const ShardRange sr = shard_range(a.g, shard, nshards);
   const size_t set_bytes = (size_t)c->nx * nr_of(c->kvar) * sizeof(T);
   a.pq0 = sr.pq0;
   a.npq = sr.npq;
   if (mode == 0) {
-    // partial reductions of this launch shape and arithmetic (all chunks when sharded): the buffer grows to the
-    // largest one used
-    const size_t pbytes = (size_t)std::max(sr.sets, nshards * sr.chunk) * set_bytes;
+    // partial reductions of this launch shape and arithmetic: the buffer grows to the largest one used
+    const size_t pbytes = (size_t)sr.sets * set_bytes;
     if (c->part_bytes < pbytes) {
       lmdg::dfree(c->part);
       c->part = nullptr;
@@ -220,12 +211,6 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
   c->ev_pending = P;
   c->part_prec = P;
   if (mode == 0) {
-    if (nshards > 1) {
-      // every chunk from the other shards (the callback fills them in place, ordered on s)
-      if (!c->xfn) return LMDG_ERR_STATE;
-      if (c->xfn(c->xuser, c->part, (size_t)sr.chunk * set_bytes, nshards, X, sweep_flags(P, source, store), s) != 0)
-        return LMDG_ERR_EXCHANGE;
-    }
     // the adjoint problem has its own source (q_adj, vacuum inflow): no slope moments, no boundary terms
     CK(launch_epilogue<T>(c->kvar, c->nx, sr.sets, c->h, a.part, X, c->d64.sse, c->d64.sigt, c->qmom,
                           c->use_adj ? nullptr : c->p1ra64, c->use_adj ? nullptr : c->sq1, source, y, s));
@@ -419,7 +404,49 @@ struct GmresOut {
   int iters = 0;
   double est = 0;
   bool breakdown = false;
+  double kappa = 0;   // condition number of the cycle's Hessenberg matrix (0: no column)
 };
+
+// Condition number sigma_max / sigma_min of the k x k upper-triangular factor R (column-major, leading dimension
+// ld) that the Givens rotations leave of a GMRES cycle's (k+1) x k Hessenberg matrix (same singular values), by
+// one-sided Jacobi (Hestenes): plane rotations of column pairs until every pair is orthogonal to working
+// precision; the column norms are then the singular values.  Host arithmetic, k <= 120.
+double triangular_cond(const std::vector<double> &Rm, int ld, int k) {
+  if (k <= 0) return 0.0;
+  std::vector<double> A((size_t)k * k);
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) A[(size_t)j * k + i] = i <= j ? Rm[(size_t)j * ld + i] : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        double al = 0, be = 0, ga = 0;
+        for (int i = 0; i < k; ++i) {
+          const double ap = A[(size_t)p * k + i], aq = A[(size_t)q * k + i];
+          al += ap * ap; be += aq * aq; ga += ap * aq;
+        }
+        if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+        off = std::max(off, std::fabs(ga) / std::sqrt(al * be));
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cth = 1.0 / std::sqrt(1.0 + t * t), sth = cth * t;
+        for (int i = 0; i < k; ++i) {
+          const double ap = A[(size_t)p * k + i], aq = A[(size_t)q * k + i];
+          A[(size_t)p * k + i] = cth * ap - sth * aq;
+          A[(size_t)q * k + i] = sth * ap + cth * aq;
+        }
+      }
+    if (off <= 1e-15) break;
+  }
+  double smax = 0, smin = HUGE_VAL;
+  for (int j = 0; j < k; ++j) {
+    double nn = 0;
+    for (int i = 0; i < k; ++i) nn += A[(size_t)j * k + i] * A[(size_t)j * k + i];
+    smax = std::max(smax, std::sqrt(nn));
+    smin = std::min(smin, std::sqrt(nn));
+  }
+  return smin > 0 ? smax / smin : HUGE_VAL;
+}
 
 // One GMRES(m) cycle from a zero initial guess for K d = r, ||r|| = rnorm: d (device) receives the
 // correction Minv V y.  Stops early when the least-squares residual reaches target.
@@ -481,6 +508,7 @@ int gmres_cycle(lmdg_ctx *c, int fp32, const double *r, double rnorm, double *d,
     go->est = std::fabs(g[j + 1]);
     if (go->est <= target || invariant) { go->breakdown = invariant; break; }
   }
+  go->kappa = triangular_cond(H, m + 1, k);
   // back substitution H y = g
   std::vector<double> yv(k, 0.0);
   for (int i = k - 1; i >= 0; --i) {
@@ -531,7 +559,6 @@ const char *lmdg_strerror(int code) {
     case LMDG_ERR_TIMEOUT: return "sweep gave up waiting for an upstream strip (spin limit)";
     case LMDG_ERR_BREAKDOWN: return "non-finite residual or Krylov breakdown";
     case LMDG_ERR_STATE: return "call out of order";
-    case LMDG_ERR_EXCHANGE: return "the exchange callback of a sharded context failed";
     default: return "unknown error";
   }
 }
@@ -1009,16 +1036,6 @@ int lmdg_sweep_combine(lmdg_ctx *c, const double *x, const void *parts, double *
   return do_sweep<double>(c, x, y, src, false, 0, s, 2, 0, 1, pp);
 }
 
-int lmdg_set_shard(lmdg_ctx *c, int shard, int nshards, lmdg_exchange_fn fn, void *user) {
-  if (!c || nshards < 1 || nshards > 4096 || shard < 0 || shard >= nshards) return LMDG_ERR_ARG;
-  if (nshards > 1 && !fn) return LMDG_ERR_ARG;
-  c->shard = nshards > 1 ? shard : 0;
-  c->nshards = nshards;
-  c->xfn = nshards > 1 ? fn : nullptr;
-  c->xuser = nshards > 1 ? user : nullptr;
-  return 0;
-}
-
 int lmdg_get_psi(lmdg_ctx *c, double *psi, int flags, void *stream) {
   if (!c || !psi) return LMDG_ERR_ARG;
   if (c->psi_kind < 0) return LMDG_ERR_STATE;
@@ -1067,7 +1084,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
   };
   double rn2 = 0;
   int iters = 0, refine = 0, status = 0;
-  double r0 = 0;
+  double r0 = 0, kappa = 0;
   if (fp32 && !x0) {
     // FP32 start from zero: b from an FP32 source sweep (or, with LMDG_SOLVE_EXACT_REF, from a sweep in the
     // residual arithmetic, so that the tolerance reference ||b|| carries no FP32 error) and an FP32 GMRES cycle
@@ -1087,6 +1104,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
       const double target = std::max(c->opt.inner_tol * r0, 0.5 * c->opt.tol * r0);
       if (int e = gmres_cycle(c, 1, R, r0, D, m, target, c->opt.max_iters, &go, s)) return e;
       iters += go.iters;
+      kappa = std::max(kappa, go.kappa);
       CK(axpby(X, 1.0, D, 1.0, N, s));
     }
     if (int e = residual(&rn2)) return e;
@@ -1103,6 +1121,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     GmresOut go;
     if (int e = gmres_cycle(c, fp32, R, rn, D, m, target, c->opt.max_iters - iters, &go, s)) return e;
     iters += go.iters;
+    kappa = std::max(kappa, go.kappa);
     refine++;
     CK(axpby(X, 1.0, D, 1.0, N, s));
     if (int e = residual(&rn2)) return e;
@@ -1138,6 +1157,7 @@ int lmdg_solve(lmdg_ctx *c, const double *x0, double *x, double *phi, lmdg_stats
     st->sweeps_f32x2 = c->sweeps2;
     st->resid0 = r0;
     st->resid = rn;
+    st->kappa_est = kappa;
     st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     harvest(c, true);
     st->sweep_ms_fp64 = c->sweep_ms[0];
@@ -1233,7 +1253,6 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
   if (!c || !g) return LMDG_ERR_ARG;
   if (c->variant == LMDG_RLM || c->variant == LMDG_P0 || c->q_layout == 2) return LMDG_ERR_ARG;
   if (!c->rev_ok) return LMDG_ERR_QUAD;
-  if (c->nshards > 1) return LMDG_ERR_STATE;   // the correlation reads the opposite directions' stored psi
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(c->dev));
@@ -1304,6 +1323,7 @@ int lmdg_adjoint(lmdg_ctx *c, const double *g, double *dss, double *dsa, double 
     st->sweeps_fp32 = s1.sweeps_fp32 + s2.sweeps_fp32;
     st->sweeps_f32x2 = s1.sweeps_f32x2 + s2.sweeps_f32x2;
     st->resid = std::max(s1.resid / std::max(s1.resid0, 1e-300), s2.resid / std::max(s2.resid0, 1e-300));
+    st->kappa_est = std::max(s1.kappa_est, s2.kappa_est);
     st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return (st1 == LMDG_ERR_NOTCONV || st2 == LMDG_ERR_NOTCONV) ? LMDG_ERR_NOTCONV : 0;

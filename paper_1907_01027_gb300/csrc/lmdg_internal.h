@@ -241,9 +241,4 @@ struct lmdg_ctx {
   lmdg::VertexDsa dsa;                     // vertex diffusion correction (precond = 2, 3)
   double *binv = nullptr;                  // precond = 3: [nx][4][4] inverses of K's cell-diagonal blocks
   int local_mode = 0;                      // FP64 sweeps cut the upwind coupling (SweepArgs::local)
-  // angle sharding (lmdg_set_shard): this context sweeps chunk `shard` of `nshards` of the partial sets and
-  // xfn fills the other chunks before every epilogue
-  int shard = 0, nshards = 1;
-  lmdg_exchange_fn xfn = nullptr;
-  void *xuser = nullptr;
 };

@@ -15,13 +15,7 @@ VARIANTS = {"std": STD, "lm": LM, "rlm": RLM, "p0": P0}
 FP64, FP32, FP32_BF16STORE = 0, 1, 2
 SWEEP_SOURCE, SWEEP_FP32, SWEEP_STORE, HOST_PTRS, SWEEP_F32X2, SOLVE_EXACT_REF = 1, 2, 4, 8, 16, 32
 RESID_FP64, RESID_F32X2 = 0, 1
-ERR_TIMEOUT, ERR_NOTCONV, ERR_BREAKDOWN, ERR_STATE, ERR_EXCHANGE = -6, -5, -7, -8, -9
-
-
-# int (*lmdg_exchange_fn)(void *user, void *parts, size_t chunk_bytes, int nshards, const double *x, int flags,
-#                         void *stream)
-EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
-                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+ERR_TIMEOUT, ERR_NOTCONV, ERR_BREAKDOWN, ERR_STATE = -6, -5, -7, -8
 
 
 class LmdgError(RuntimeError):
@@ -51,7 +45,7 @@ class Stats(ctypes.Structure):
                 ("sweeps_fp32", ctypes.c_int), ("resid0", ctypes.c_double), ("resid", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("sweep_ms_fp64", ctypes.c_double),
                 ("sweep_ms_fp32", ctypes.c_double), ("launches", ctypes.c_longlong),
-                ("sweeps_f32x2", ctypes.c_int), ("sweep_ms_f32x2", ctypes.c_double)]
+                ("sweeps_f32x2", ctypes.c_int), ("sweep_ms_f32x2", ctypes.c_double), ("kappa_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,7 +81,6 @@ def _lib():
             "lmdg_shard_layout": ([vp, ip, ip, vp, vp, vp], ip),
             "lmdg_sweep_shard": ([vp, vp, vp, ip, ip, ip, vp], ip),
             "lmdg_sweep_combine": ([vp, vp, vp, vp, ip, vp], ip),
-            "lmdg_set_shard": ([vp, ip, ip, EXCHANGE_FN, vp], ip),
             "lmdg_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
@@ -216,7 +209,7 @@ class Context:
         self._check(rc, "lmdg_solve", allow=(ERR_NOTCONV, ERR_BREAKDOWN) if allow_stall else (ERR_NOTCONV,))
         return x, phi, st.as_dict(), rc
 
-    # ---- angle sharding (lmdg_shard_layout, lmdg_sweep_shard, lmdg_sweep_combine, lmdg_set_shard)
+    # ---- angle sharding (lmdg_shard_layout, lmdg_sweep_shard, lmdg_sweep_combine)
     def shard_layout(self, nshards, flags=0):
         """(sets, sets per chunk, bytes per chunk) of the partial sets for the arithmetic of ``flags``."""
         sets, chunk = ctypes.c_int(0), ctypes.c_int(0)
@@ -237,16 +230,6 @@ class Context:
         self._check(self.lib.lmdg_sweep_combine(self.h, x.data_ptr(), parts.data_ptr(), y.data_ptr(), flags,
                                                 _stream()), "lmdg_sweep_combine")
         return y
-
-    def set_shard(self, shard, nshards, fn=None):
-        """lmdg_set_shard.  ``fn(parts_ptr, chunk_bytes, nshards, x_ptr, flags, stream) -> int`` fills the other
-        chunks (see ``paper_1907_01027_gb300.shard``); the context keeps the callback alive."""
-        if nshards > 1 and fn is None:
-            raise ValueError("a sharded context needs an exchange callback")
-        cb = EXCHANGE_FN(lambda user, parts, nbytes, n, x, flags, stream: int(fn(parts, nbytes, n, x, flags,
-                                                                                  stream))) if fn else EXCHANGE_FN()
-        self._check(self.lib.lmdg_set_shard(self.h, shard, nshards, cb, None), "lmdg_set_shard")
-        self._exchange_cb = cb
 
     def get_psi(self):
         per = 4 if self.variant == STD else 1

@@ -4,9 +4,8 @@ The sweep is independent per direction (Section 2.1.1: L is block diagonal over 
 angular reduction couples the directions.  The library forms a sweep's reduction from partial sets, one per
 (quadrant, direction group) of its launch shape, and sums them in a fixed order in the epilogue.  Sharding splits
 the sets into one contiguous chunk per rank (``lmdg_shard_layout``): each rank sweeps the whole mesh for the
-directions of its chunk, the ranks all-gather the chunks in place (the exchange callback of ``lmdg_set_shard``),
-and every rank runs the same epilogue, so the result is bitwise the one GPU's.  GMRES vectors are replicated (every
-rank runs the same iterations on the same data); the stored angular unknowns are sharded by direction.
+directions of its chunk, the ranks all-gather the chunks in place, and every rank runs the same epilogue, so the
+result is bitwise the one GPU's.  The stored angular unknowns of a storing sweep are sharded by direction.
 
 Only argument marshalling and the collective live here; every sweep and epilogue runs in the library's kernels.
 """
@@ -29,40 +28,22 @@ def all_gather_chunks(buf, chunk_numel, rank, world, group=None):
     dist.all_gather_into_tensor(buf[:world * chunk_numel], mine, group=group)
 
 
-class _DeviceBytes:
-    """A device allocation of the library seen by torch as a uint8 tensor (no copy)."""
-
-    def __init__(self, ptr, nbytes):
-        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
-
-
-def attach(ctx, group=None):
-    """Shard ``ctx`` (a :class:`~paper_1907_01027_gb300.lmdg.Context` on this rank's GPU, set up with the same
-    problem and options on every rank) over the ranks of ``group``: every later sweep of the context -- ``sweep``,
-    ``solve`` and its recovery sweep -- sweeps this rank's chunk of the directions and all-gathers the partial sets
-    before its epilogue.  Returns (rank, world)."""
+def sharded_sweep(ctx, x, y=None, flags=0, group=None):
+    """One application of the reduced operator -- lmdg_sweep's y = K x, or K x - b with SWEEP_SOURCE -- with the
+    directions split across the ranks of ``group`` (default: the world), one GPU per rank: this rank sweeps its
+    chunk of the partial sets (``lmdg_sweep_shard``), the chunks are all-gathered in place, and the epilogue
+    (``lmdg_sweep_combine``) gives every rank the bits one GPU's ``lmdg_sweep`` gives.  ``ctx`` is this rank's
+    :class:`~paper_1907_01027_gb300.lmdg.Context` of the problem (set up with the same arguments on every rank);
+    ``x`` a CUDA tensor [N][4] of float64, the same on every rank."""
     import torch
     import torch.distributed as dist
     rank, world = dist.get_rank(group), dist.get_world_size(group)
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    def exchange(parts, chunk_bytes, nshards, x, flags, stream):
-        try:
-            buf = torch.as_tensor(_DeviceBytes(parts, nshards * chunk_bytes), device=dev)
-            st = torch.cuda.ExternalStream(stream, device=dev) if stream else torch.cuda.default_stream(dev)
-            with torch.cuda.stream(st):
-                all_gather_chunks(buf, chunk_bytes, rank, nshards, group)
-            return 0
-        except Exception:   # reported to the caller of the sweep as LMDG_ERR_EXCHANGE
-            return 1
-
-    ctx.set_shard(rank, world, exchange if world > 1 else None)
-    return rank, world
+    _, _, nbytes = ctx.shard_layout(world, flags)
+    parts = torch.empty(world * nbytes, dtype=torch.uint8, device=x.device)
+    ctx.sweep_shard(x, parts, rank, world, flags)
+    if world > 1:
+        all_gather_chunks(parts, nbytes, rank, world, group)
+    return ctx.sweep_combine(x, parts, y, flags)
 
 
-def detach(ctx):
-    """Undo :func:`attach`: the context sweeps every direction again."""
-    ctx.set_shard(0, 1)
-
-
-__all__ = ["chunk_range", "all_gather_chunks", "attach", "detach"]
+__all__ = ["chunk_range", "all_gather_chunks", "sharded_sweep"]

@@ -64,8 +64,7 @@ def test_binding_layouts_match_header(tmp_path):
               "LMDG_SWEEP_FP32": L.SWEEP_FP32, "LMDG_SWEEP_STORE": L.SWEEP_STORE, "LMDG_HOST_PTRS": L.HOST_PTRS,
               "LMDG_SWEEP_F32X2": L.SWEEP_F32X2, "LMDG_SOLVE_EXACT_REF": L.SOLVE_EXACT_REF,
               "LMDG_RESID_FP64": L.RESID_FP64, "LMDG_RESID_F32X2": L.RESID_F32X2,
-              "LMDG_ERR_TIMEOUT": L.ERR_TIMEOUT, "LMDG_ERR_NOTCONV": L.ERR_NOTCONV, "LMDG_ERR_STATE": L.ERR_STATE,
-              "LMDG_ERR_EXCHANGE": L.ERR_EXCHANGE}
+              "LMDG_ERR_TIMEOUT": L.ERR_TIMEOUT, "LMDG_ERR_NOTCONV": L.ERR_NOTCONV, "LMDG_ERR_STATE": L.ERR_STATE}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "lmdg.h"', "int main(void) {"]
     for cname, py in structs.items():
         src.append(f'  printf("size {cname} %zu\\n", sizeof({cname}));')

@@ -165,3 +165,20 @@ def test_storing_sweep_psi_multistrip(n):
     ctx.sweep(x, flags=SWEEP_SOURCE | SWEEP_STORE | SWEEP_FP32)
     assert rel(ctx.get_psi(), ref) < 1e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_kappa_estimate_from_the_hessenberg(variant):
+    """lmdg_stats.kappa_est, the condition number of a GMRES cycle's Hessenberg matrix, is a lower estimate of the
+    condition number of the (here unpreconditioned) reduced operator, from the oracle's dense operator, and reaches
+    it as the Krylov space fills (100 unknowns, one cycle of up to 100 iterations driven to stagnation)."""
+    p = random_problem(5, 4, 0.3, 71, alpha=False, q_per_angle=False)
+    so = SweepOracle(p)
+    n = 4 * p.nx
+    K = np.stack([so.K(variant, e.reshape(p.nx, 4)).ravel() for e in np.eye(n)], axis=1)
+    cond = np.linalg.cond(K)
+    ctx = _ctx(p, variant, precond=0, restart=n, tol=1e-15, max_iters=n)
+    _, _, st, _ = ctx.solve(allow_stall=True)
+    ctx.close()
+    assert st["kappa_est"] <= cond * (1 + 1e-6), (st["kappa_est"], cond)
+    assert st["kappa_est"] >= 0.5 * cond, (st["kappa_est"], cond, st["iters"])
