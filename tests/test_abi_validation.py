@@ -156,3 +156,26 @@ def test_mesh_and_alpha_layout_validated(L):
                           arrs[4].ctypes.data, arrs[5].ctypes.data, 1, None if a is None else a.ctypes.data, lay,
                           1.0, 0, None)
         assert rc == -1, (nx, ny, lay)
+
+
+def test_shard_entry_points_reject_bad_arguments(L):
+    """The angle-sharding calls check their arguments on the host before any device work: a missing context or
+    buffer, a shard outside [0, nshards), nshards outside [1, 4096], host pointers, and float-float with FP32."""
+    import ctypes as ct
+    sets, chunk = ct.c_int(0), ct.c_int(0)
+    nbytes = ct.c_size_t(0)
+    assert L.lmdg_shard_layout(None, 0, 2, ct.byref(sets), ct.byref(chunk), ct.byref(nbytes)) == -1
+    buf = (ct.c_double * 8)()
+    assert L.lmdg_sweep_shard(None, buf, buf, 0, 2, 0, None) == -1
+    assert L.lmdg_sweep_combine(None, buf, buf, buf, 0, None) == -1
+    fake = ct.c_void_p(1)   # never dereferenced: each call below fails its checks before it touches the context
+    assert L.lmdg_shard_layout(fake, 0, 0, None, None, None) == -1
+    assert L.lmdg_shard_layout(fake, 0, 4097, None, None, None) == -1
+    assert L.lmdg_shard_layout(fake, 2 | 16, 2, None, None, None) == -1       # FP32 and float-float
+    assert L.lmdg_sweep_shard(fake, buf, buf, 2, 2, 0, None) == -1            # shard >= nshards
+    assert L.lmdg_sweep_shard(fake, buf, buf, -1, 2, 0, None) == -1
+    assert L.lmdg_sweep_shard(fake, buf, None, 0, 2, 0, None) == -1           # no partial buffer
+    assert L.lmdg_sweep_shard(fake, buf, buf, 0, 2, 8, None) == -1            # host pointers
+    assert L.lmdg_sweep_shard(fake, buf, buf, 0, 2, 16 | 4, None) == -1       # float-float storing
+    assert L.lmdg_sweep_combine(fake, buf, buf, buf, 4, None) == -1           # storing flag
+    assert L.lmdg_sweep_combine(fake, buf, buf, buf, 2 | 16, None) == -1
