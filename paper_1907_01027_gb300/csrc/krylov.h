@@ -35,8 +35,8 @@ cudaError_t block_step(double *y, const double *x, const double *binv, const dou
                        cudaStream_t s);
 // p[0..N) = v
 cudaError_t fill_u32(unsigned *p, unsigned v, size_t N, cudaStream_t s);
-// stored psi (column-major per direction, kind 0 double, 1 float, 2 bfloat16; per values per cell) to the user
-// layout [u][nj*ni][per] in double; N = directions * ni * nj * per
+// stored psi (one wavefront-ordered plane per direction, psi_slot; kind 0 double, 1 float, 2 bfloat16; per values
+// per slot) to the user layout [u][nj*ni][per] in double; perm maps sorted to user directions, nq per quadrant
 cudaError_t psi_to_user(double *y, const void *x, int kind, int per, int ni, int nj, int nang, int nq, const int *perm,
                         cudaStream_t s);
 }  // namespace lmdg
