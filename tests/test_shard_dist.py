@@ -153,3 +153,53 @@ def test_sharded_apply_is_bitwise_the_single_process_one(variant, ws, groups):
     assert np.abs(single - ref).max() <= 1e-13 * np.abs(ref).max()
     for rank, y in _spawn(_sharded_apply_worker, ws, variant, groups):
         assert np.array_equal(y, single), rank
+
+
+# ------------------------------------------------------------------ shard.sharded_sweep on gloo ranks
+class _OracleShardContext:
+    """Stands in for a Context in shard.sharded_sweep on the CPU: the same three calls (layout, one chunk's partial
+    sets into a byte buffer, the combine), their arithmetic done by the oracle (test infrastructure only)."""
+
+    def __init__(self, variant, groups):
+        from oracle.sweeps import SweepOracle
+        self.p = _problem()
+        self.so = SweepOracle(self.p, threads=1)
+        self.variant = variant
+        self.sets = _sets(self.p, groups)
+
+    def shard_layout(self, nshards, flags=0):
+        chunk = -(-len(self.sets) // nshards)
+        return len(self.sets), chunk, chunk * self.p.nx * 4 * 8
+
+    def sweep_shard(self, x, parts, shard, nshards, flags=0):
+        _, chunk, _ = self.shard_layout(nshards)
+        view = parts.view(torch.float64).view(nshards * chunk, self.p.nx, 4).numpy()
+        first, count = chunk_range(len(self.sets), nshards, shard)
+        X = x.numpy()
+        for s in range(first, first + count):
+            view[s] = _partial(self.so, self.variant, self.sets[s], X)
+
+    def sweep_combine(self, x, parts, y=None, flags=0):
+        view = parts.view(torch.float64).view(-1, self.p.nx, 4).numpy()
+        return torch.from_numpy(_combine(self.so, self.variant, x.numpy(), view, len(self.sets)))
+
+
+def _sharded_sweep_worker(rank, ws, port, q, variant, groups):
+    _init(rank, ws, port)
+    from paper_1907_01027_gb300.shard import sharded_sweep
+    ctx = _OracleShardContext(variant, groups)
+    x = torch.from_numpy(np.random.default_rng(5).standard_normal((ctx.p.nx, 4)))
+    q.put((rank, sharded_sweep(ctx, x).numpy()))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("variant", ["std", "lm"])
+@pytest.mark.parametrize("ws,groups", [(2, 2), (3, 1)])
+def test_sharded_sweep_helper_on_gloo_ranks(variant, ws, groups):
+    """paper_1907_01027_gb300.shard.sharded_sweep itself (layout, this rank's chunk, in-place all-gather, combine)
+    across ranks: every rank gets the single process's bits."""
+    ctx = _OracleShardContext(variant, groups)
+    X = np.random.default_rng(5).standard_normal((ctx.p.nx, 4))
+    single = _combine(ctx.so, variant, X, [_partial(ctx.so, variant, d, X) for d in ctx.sets], len(ctx.sets))
+    for rank, y in _spawn(_sharded_sweep_worker, ws, variant, groups):
+        assert np.array_equal(y, single), rank
