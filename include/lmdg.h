@@ -291,14 +291,19 @@ int lmdg_shard_layout(const lmdg_ctx *ctx, int flags, int nshards, int *sets, in
 
 /* Sweep the directions of chunk `shard` of nshards at x (DEVICE [N][4]) and write their partial sets into chunk
  * `shard` of parts (DEVICE, nshards * chunk_bytes bytes, 16-byte aligned; the other chunks are not touched).
- * flags: LMDG_SWEEP_SOURCE, LMDG_SWEEP_FP32 or LMDG_SWEEP_F32X2, LMDG_SWEEP_STORE (this shard's directions only);
- * LMDG_HOST_PTRS returns LMDG_ERR_ARG.  Synchronises the stream (reads the sweep's error word). */
+ * flags: LMDG_SWEEP_SOURCE, LMDG_SWEEP_FP32 or LMDG_SWEEP_F32X2, LMDG_SWEEP_STORE (stores this shard's directions
+ * only: lmdg_get_psi then returns them, the other directions' entries being whatever the context held before);
+ * LMDG_HOST_PTRS returns LMDG_ERR_ARG, and so does float-float with FP32 or with storing.  Errors: LMDG_ERR_ARG
+ * (NULL pointers, shard outside [0, nshards), nshards outside [1, 4096]), LMDG_ERR_TIMEOUT, LMDG_ERR_CUDA,
+ * LMDG_ERR_NOMEM (the stored unknowns).  Synchronises the stream (reads the sweep's error word). */
 int lmdg_sweep_shard(lmdg_ctx *ctx, const double *x, void *parts, int shard, int nshards, int flags,
                      void *stream);
 
 /* The epilogue of lmdg_sweep from a complete partial buffer (every chunk written by lmdg_sweep_shard, here or on
  * other GPUs): y = K x, or K x - b with LMDG_SWEEP_SOURCE, as lmdg_sweep gives for the same flags; x, parts, y
- * DEVICE pointers.  Asynchronous on stream. */
+ * DEVICE pointers (parts as laid out by lmdg_shard_layout for these flags; a chunk not written holds whatever the
+ * buffer held).  LMDG_ERR_ARG for NULL pointers, host pointers, LMDG_SWEEP_STORE, or float-float with FP32.
+ * Asynchronous on stream. */
 int lmdg_sweep_combine(lmdg_ctx *ctx, const double *x, const void *parts, double *y, int flags, void *stream);
 
 /* Problem sizes of a context: cells along x and y, n_Omega, variant (any pointer may be NULL). */
