@@ -206,7 +206,10 @@ int do_sweep(lmdg_ctx *c, const double *X, double *y, int source, bool store, in
     c->ytr_prec = want;
   }
   CK(cudaEventRecord(c->ev0, s));
-  if (a.npq > 0) CK(launch_sweep<T>(c->kvar, a, s));   // a shard beyond the last set sweeps nothing
+  // a shard beyond the last set sweeps nothing; its error word is cleared all the same, so that the check after the
+  // call does not report an earlier sweep's error
+  if (a.npq > 0) CK(launch_sweep<T>(c->kvar, a, s));
+  else CK(cudaMemsetAsync(c->ctrl, 0, 2 * sizeof(unsigned), s));
   CK(cudaEventRecord(c->ev1, s));
   c->ev_pending = P;
   c->part_prec = P;
