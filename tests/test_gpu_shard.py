@@ -72,8 +72,8 @@ def test_repeated_shard_applications_stay_bitwise(variant, mode):
 
 
 def test_sharded_sweep_on_one_rank():
-    """The torch.distributed path of paper_1907_01027_gb300.shard.sharded_sweep on a process group of one rank (every
-    call of this build has one GPU): one chunk, the combine, lmdg_sweep's bits."""
+    """The torch.distributed path of paper_1907_01027_gb300.shard.sharded_sweep on a process group of one rank (this
+    test runs on one GPU): one chunk, the combine, lmdg_sweep's bits."""
     import os
     import socket
     import torch
